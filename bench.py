@@ -1,0 +1,358 @@
+#!/usr/bin/env python
+"""Benchmark: point-edge tests/s and points classified/s of pip_classify on one GB300.
+
+Workload (N = 1): the 1M building-footprint batch -- 1,000,000 polygons (log-normal 4-64
+vertices, mean ~7), 16 candidate points per polygon (16M candidates), int32 1e-7-degree
+coordinates in Ghana's lon/lat box; synthetic and seeded.  One step = one pip_classify call
+over the whole batch (all steps of the method: candidate fetch, edge staging and local
+frame, straddle test, FP32 side test with exact fallback, parity, ballot pack).  Under
+torchrun each rank classifies its own batch (seed + rank): weak scaling, no collective on
+the data path.  The inputs (~258 MB) exceed the 129 MB L2, so no flush is needed between
+steps.
+
+Printed JSON line: value = pair tests/s over the whole job (device-timed, inputs resident);
+e2e = the same metric through the public API with host buffers (H2D of every input and D2H
+of the bits inside the timed region); roofline of the classify kernel against measured HBM
+bandwidth; the CPU oracle as the baseline; SM clocks sampled during the timed region.
+
+``--impl reference`` times the CPU oracle (the reference implementation of the method in
+this repository) on a bounded sample of the same workload and prints the same line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "point-edge tests/s and points classified/s (1 GB300), % of roofline, 0 mismatches"
+UNIT = "pair-tests/s"
+
+
+def _env_int(k, d):
+    try:
+        return int(os.environ.get(k, d))
+    except ValueError:
+        return d
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons, sampled every 200 ms in the background."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self._t = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200",
+                 "-i", str(self.gpu)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, ValueError):
+            self.proc = None
+            return
+        self._t = threading.Thread(target=self._read, daemon=True)
+        self._t.start()
+        time.sleep(0.25)
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append((time.time(), line.strip()))
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for _, ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def oracle_baseline(w, target_s=10.0, max_reps=20):
+    """The CPU oracle on the whole batch, repeated until ~target_s of CPU work."""
+    import oracle
+    threads = oracle.default_threads()
+    oracle.build()
+    reps, t_total = 0, 0.0
+    while reps < max_reps and (t_total < target_s or reps == 0):
+        t0 = time.perf_counter()
+        oracle.classify(w.points, w.poly_offsets, w.verts, w.cand_offsets, w.cand_ids, threads=threads)
+        t_total += time.perf_counter() - t0
+        reps += 1
+    T = w.pair_tests()
+    return {"value": T * reps / t_total, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"whole {w.name} batch ({w.n_polys} polygons, {w.n_candidates} candidates, "
+                      f"{T} pair tests) x {reps} runs, {t_total:.1f} s",
+            "points_per_s": w.n_candidates * reps / t_total}
+
+
+def make_workload(name, rank, scale):
+    from paper_2306_04316_gb300 import workloads as W
+    if name == "footprints":
+        return W.footprints(seed=W.BASE_SEED + 2 + 1000 * rank, n_polys=int(1_000_000 * scale))
+    if name == "stress":
+        return W.stress(seed=W.BASE_SEED + 5 + 1000 * rank, n_polys=int(1_000_000 * scale))
+    if name == "star":
+        return W.star(seed=W.BASE_SEED + 1 + 1000 * rank)
+    raise SystemExit(f"unknown workload {name}")
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    import oracle
+    oracle.build()
+    w = make_workload(args.workload, 0, 1.0)
+    # a bounded sample: the first polygons of the batch, sized so that warm-up plus timed
+    # steps take about two minutes of CPU work in total
+    threads = oracle.default_threads()
+    t0 = time.perf_counter()
+    oracle.classify(w.points, w.poly_offsets, w.verts, w.cand_offsets, w.cand_ids, threads=threads)
+    t_full = time.perf_counter() - t0
+    frac = min(1.0, 120.0 / max(1e-9, (args.steps + args.warmup) * t_full))
+    sub = w.prefix(max(1, int(w.n_polys * frac)))
+    steps_t = []
+    for i in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        oracle.classify(sub.points, sub.poly_offsets, sub.verts, sub.cand_offsets, sub.cand_ids, threads=threads)
+        dt = time.perf_counter() - t0
+        if i >= args.warmup:
+            steps_t.append(dt)
+    T = sub.pair_tests()
+    tot = sum(steps_t)
+    value = T * len(steps_t) / tot
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * tot / len(steps_t),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
+            "data": "synthetic", "config": {"workload": f"{w.name}: {w.n_polys} polygons, {w.n_candidates} candidates",
+                                             "pair_tests_per_step": T, "l2": "inputs larger than L2"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                             "sample": f"first {sub.n_polys} of {w.n_polys} {w.name} polygons per step "
+                                       f"({sub.n_candidates} candidates, {T} pair tests)"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "points_per_s": sub.n_candidates * len(steps_t) / tot}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="footprints", choices=["footprints", "stress", "star"])
+    ap.add_argument("--kernel", default="filtered", choices=["filtered", "exact"])
+    ap.add_argument("--scale", type=float, default=1.0, help="fraction of the full batch (tests only)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=20)
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+
+    rank = _env_int("RANK", 0)
+    world = _env_int("WORLD_SIZE", 1)
+    local = _env_int("LOCAL_RANK", 0)
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import numpy as np
+    import torch
+    from paper_2306_04316_gb300 import api, build as pbuild
+
+    pbuild.build_library()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    w = make_workload(args.workload, rank, args.scale)
+    T = w.pair_tests()
+    B = w.algorithmic_bytes()
+    d = api.to_device(w)
+    n_words = w.n_words
+    out = torch.empty(n_words, dtype=torch.int32, device="cuda")
+    fn = api.pip_classify if args.kernel == "filtered" else api.pip_classify_exact
+    cand_o, cand_i = d.get("cand_offsets"), d.get("cand_ids")
+
+    def step():
+        fn(d["points"], d["poly_offsets"], d["verts"], cand_o, cand_i, out=out)
+
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    sampler = ClockSampler(local)
+    sampler.start()
+    ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    for i in range(args.steps):
+        ev0[i].record(stream)
+        step()
+        ev1[i].record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clocks = sampler.stop()
+    per = [ev0[i].elapsed_time(ev1[i]) for i in range(args.steps)]
+    total_ms = ev0[0].elapsed_time(ev1[-1])
+    t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
+    if dist:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    total_ms = float(t.item())
+    ms_step = total_ms / args.steps
+    kern_ms = statistics.mean(per)
+
+    # the other kernel on the same batch (comparison), a short run
+    other_fn = api.pip_classify_exact if args.kernel == "filtered" else api.pip_classify
+    other_ms = None
+    if rank == 0:
+        for _ in range(3):
+            other_fn(d["points"], d["poly_offsets"], d["verts"], cand_o, cand_i, out=out)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        n_o = max(5, min(200, args.steps))
+        e0.record(stream)
+        for _ in range(n_o):
+            other_fn(d["points"], d["poly_offsets"], d["verts"], cand_o, cand_i, out=out)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        other_ms = e0.elapsed_time(e1) / n_o
+
+    # e2e: host buffers through the public API (pinned H2D of every input, D2H of the bits)
+    e2e = None
+    if not args.no_e2e:
+        host = {k: torch.from_numpy(getattr(w, k)).pin_memory() for k in ("points", "poly_offsets", "verts")}
+        if not w.dense:
+            host["cand_offsets"] = torch.from_numpy(w.cand_offsets).pin_memory()
+            host["cand_ids"] = torch.from_numpy(w.cand_ids).pin_memory()
+        hout = torch.empty(n_words, dtype=torch.int32).pin_memory()
+        h2d = sum(t_.numel() * t_.element_size() for t_ in host.values())
+        d2h = hout.numel() * 4
+
+        def e2e_step():
+            for k_, v_ in host.items():
+                d[k_].copy_(v_, non_blocking=True)
+            fn(d["points"], d["poly_offsets"], d["verts"], d.get("cand_offsets"), d.get("cand_ids"), out=out)
+            hout.copy_(out, non_blocking=True)
+
+        for _ in range(3):
+            e2e_step()
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.e2e_steps):
+            e2e_step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        te = torch.tensor([e0.elapsed_time(e1)], dtype=torch.float64, device="cuda")
+        if dist:
+            dist.all_reduce(te, op=dist.ReduceOp.MAX)
+        e2e_ms = float(te.item()) / args.e2e_steps
+        e2e = {"value": T * world / (e2e_ms / 1000.0), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(d2h), "ms_per_step": e2e_ms}
+
+    peaks, peak_kind = measured_peaks()
+    props = torch.cuda.get_device_properties(local)
+    n_sm = props.multi_processor_count
+    f_max = float(peaks.get("sm_max_mhz", 2070.0)) * 1e6
+    pair_peak = n_sm * 128 * f_max / 4.0
+    t_hbm = B / (float(peaks["hbm_gbs"]) * 1e9)
+    t_alu = T / pair_peak
+    bound = "hbm" if t_hbm >= t_alu else "alu"
+    achieved_gbs = B / (kern_ms / 1000.0) / 1e9
+    achieved_pairs = T / (kern_ms / 1000.0)
+    if bound == "hbm":
+        roof = {"bound": "hbm", "achieved": achieved_gbs, "peak": float(peaks["hbm_gbs"]), "unit": "GB/s",
+                "frac": achieved_gbs / float(peaks["hbm_gbs"]), "traffic": None,
+                "peak_source": peak_kind, "kernel": "k_pip_filtered" if args.kernel == "filtered" else "k_pip_exact",
+                "algorithmic_bytes": B, "kernel_ms": kern_ms}
+    else:
+        roof = {"bound": "alu", "achieved": achieved_pairs / 1e12, "peak": pair_peak / 1e12,
+                "unit": "Tpair/s", "frac": achieved_pairs / pair_peak, "traffic": None,
+                "peak_source": f"{n_sm} SMs x 128 lanes x {f_max / 1e6:.0f} MHz / 4 lane-instructions per pair",
+                "kernel": "k_pip_filtered" if args.kernel == "filtered" else "k_pip_exact",
+                "algorithmic_bytes": B, "kernel_ms": kern_ms}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = oracle_baseline(w)
+
+    if rank == 0:
+        stats = api.pip_get_stats()
+        line = {
+            "metric": METRIC, "value": T * world / (ms_step / 1000.0), "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32+i64" if args.kernel == "filtered" else "i64",
+            "data": "synthetic",
+            "config": {"workload": f"{w.name}: {w.n_polys} polygons, {w.n_candidates} candidates, "
+                                   f"{w.verts.shape[0]} vertices", "pair_tests_per_step": T,
+                       "algorithmic_bytes_per_step": B, "kernel": args.kernel,
+                       "tuning": list(api.pip_get_tuning()), "l2": "inputs larger than L2 (no flush)"},
+            "points_per_s": w.n_candidates * world / (ms_step / 1000.0),
+            "roofline": roof,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": args.steps,
+            "clocks": clocks,
+            "other_kernel": {"kernel": "exact" if args.kernel == "filtered" else "filtered",
+                             "ms_per_step": other_ms,
+                             "value": (T / (other_ms / 1000.0)) if other_ms else None},
+            "fallback_fraction": (stats["fallback_points"] / stats["candidates"]) if stats["candidates"] else None,
+        }
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

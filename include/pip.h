@@ -1,0 +1,174 @@
+/*
+ * pip.h -- C ABI of libpip: GB300 (sm_103a) point-in-polygon classification by the
+ * vector-geometric ray-casting method (Schwinger et al., "Point in polygon calculation
+ * using vector geometric methods with application to geospatial data").
+ *
+ * The method (Method section, the seven-step algorithm with Constraint 1): cast the ray
+ * d = (1, 0) from the query point p; f(r) = (r - p) . (0, 1) = r_y - p_y; an edge
+ * R_i -> R_{i+1} is a candidate crossing when f changes sign along it (steps 2-4); it is
+ * counted when p lies on the left of the edge, i.e. when (p - R_i) . n has the counting
+ * sign for the edge normal n = (d_y, -d_x) oriented so that n_x >= 0 (Constraint 1,
+ * Eq. (normal form of a line)); p is inside when the count is odd (step 7).
+ *
+ * Boundary rule (fixed, half-open; the paper's text is ambiguous at vertices and edges
+ * lying on the ray): a vertex with y_i = p_y counts as lying below the ray, and an edge is
+ * counted only when the crossing lies strictly to the right of p.  Every point therefore
+ * has exactly one answer: that of p + (eps, delta), 0 < delta << eps, under the even-odd
+ * rule.  Points on a bottom or left edge are inside, on a top or right edge outside.
+ *
+ * Data (all int32, fixed point; the intended unit is 1e-7 degree):
+ *   points        device, int32 [n_points][2] interleaved (x, y); 8-byte aligned.
+ *   poly_offsets  device, int32 [n_polys + 1], non-decreasing: polygon k owns vertices
+ *                 verts[poly_offsets[k] .. poly_offsets[k+1]).  Edges are i -> (i+1) mod m,
+ *                 so the closing edge is implicit; a repeated closing vertex R_n = R_0 (the
+ *                 paper's convention) is allowed and changes nothing.  m < 3 gives all 0.
+ *                 Self-intersecting polygons follow the even-odd rule.
+ *   verts         device, int32 [V][2] interleaved (x, y); 8-byte aligned.
+ *   cand_offsets, cand_ids
+ *                 device CSR of candidate points: polygon k's candidates are
+ *                 cand_ids[cand_offsets[k] .. cand_offsets[k+1]) (cand_offsets
+ *                 non-decreasing, cand_offsets[0] = 0, ids in [0, n_points)).  Both NULL
+ *                 selects DENSE mode: every point against every polygon.
+ *   out_bits      device, uint32.  CSR mode: ceil(C / 32) words, C = cand_offsets[n_polys];
+ *                 bit c (word c >> 5, bit c & 31, LSB first) = "point cand_ids[c] is inside
+ *                 the polygon that owns candidate c".  Dense mode: n_polys * W words,
+ *                 W = ceil(n_points / 32); bit k*32*W + j = "point j is inside polygon k".
+ *                 Every word is overwritten (bits past the last candidate are 0).
+ *   stream        a cudaStream_t passed as void* (NULL = the legacy default stream).
+ *
+ * Ownership and errors: the caller owns every buffer.  Calls are asynchronous on `stream`
+ * and never synchronise it; they check host-visible arguments only (NULL, sizes,
+ * alignment) and return PIP_OK or a negative PIP_ERR_* code without launching anything.
+ * The contents of device arrays (monotone offsets, ids in range) are checked only by
+ * pip_validate.  The library owns a small per-device workspace (work counters and
+ * statistics), created on the first call made outside stream capture; a call made during
+ * capture before the workspace exists returns PIP_ERR_WORKSPACE.  Calls on different
+ * streams that overlap on the GPU share the statistics counters only.
+ */
+#ifndef PIP_H
+#define PIP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PIP_OK              0
+#define PIP_ERR_NULL       -1   /* a required pointer is NULL (or only one CSR array given) */
+#define PIP_ERR_SIZE       -2   /* negative size, or a capacity too small */
+#define PIP_ERR_ALIGN      -3   /* points / verts not 8-byte aligned, ids not 4-byte aligned */
+#define PIP_ERR_TOO_LARGE  -4   /* a count that int32 offsets or ids cannot address */
+#define PIP_ERR_WORKSPACE  -5   /* workspace missing or too small during stream capture */
+#define PIP_ERR_CUDA       -6   /* a CUDA runtime call failed (see pip_last_cuda_error) */
+#define PIP_ERR_INVALID    -7   /* invalid tuning value */
+
+/* Counters accumulated on the device since the last pip_reset_stats. */
+typedef struct pip_stats {
+    uint64_t candidates;       /* candidates classified by pip_classify */
+    uint64_t bbox_rejects;     /* candidates outside their polygon's bounding box */
+    uint64_t fallback_points;  /* candidates re-tested exactly because an FP32 sign was
+                                  within the forward-error bound of zero */
+    uint64_t fallback_edges;   /* edges whose FP32 sign was within the bound (re-tested) */
+    uint64_t exact_candidates; /* candidates classified by pip_classify_exact */
+} pip_stats;
+
+/*
+ * pip_classify -- the FP32-filtered persistent kernel (Method, steps 2-7; Constraint 1).
+ * Each polygon is rebased to a local frame; the side test (p - R_i) . n runs in FP32 with
+ * a proven forward-error bound, and any (point, edge) pair whose FP32 value lies within
+ * the bound is re-tested exactly with 64/128-bit integers, so the result is exact.
+ * Arguments and output layout as described above.  Returns PIP_OK or PIP_ERR_*.
+ */
+int pip_classify(const int32_t *points, int64_t n_points,
+                 const int32_t *poly_offsets, const int32_t *verts, int32_t n_polys,
+                 const int32_t *cand_offsets, const int32_t *cand_ids,
+                 uint32_t *out_bits, void *stream);
+
+/*
+ * pip_classify_exact -- the plain exact kernel (same arguments and output): every
+ * (point, edge) pair tests the straddle in int32 and the side of the edge with 64-bit
+ * integer products (128-bit when a coordinate difference reaches 2^31).  The reference
+ * formulation against which the filtered kernel is compared.
+ */
+int pip_classify_exact(const int32_t *points, int64_t n_points,
+                       const int32_t *poly_offsets, const int32_t *verts, int32_t n_polys,
+                       const int32_t *cand_offsets, const int32_t *cand_ids,
+                       uint32_t *out_bits, void *stream);
+
+/*
+ * Uniform-grid binning (not in the paper; it builds the candidate CSR of a spatial join):
+ * candidates of polygon k = every point inside k's CLOSED bounding box, listed in a fixed
+ * order (grid cells row-major over the box, ascending point id within a cell), so that
+ * repeated calls on the same data give identical arrays.
+ *
+ * pip_bin_workspace_bytes returns the size of the caller-owned scratch buffer that both
+ * binning calls need for n_points points and n_polys polygons.
+ *
+ * pip_bin_count: bins the points (cell size `cell_size` units; 0 = chosen on the device
+ * from the mean polygon extent, capped so that the grid has at most 2^22 cells), then
+ * writes cand_offsets [n_polys + 1] (device, exclusive prefix sum of the per-polygon
+ * counts) and *d_total (device int64) = the number of candidates.  The grid stays in the
+ * workspace for pip_bin_fill.
+ *
+ * pip_bin_fill: writes cand_ids (device, capacity `capacity` ids) from the same inputs and
+ * workspace.  If the total exceeds `capacity`, ids past the capacity are dropped and
+ * *d_overflow (device int32, may be NULL) is set to 1; otherwise it is set to 0.
+ */
+size_t pip_bin_workspace_bytes(int64_t n_points, int32_t n_polys);
+int pip_bin_count(const int32_t *points, int64_t n_points,
+                  const int32_t *poly_offsets, const int32_t *verts, int32_t n_polys,
+                  int32_t cell_size, void *workspace, size_t workspace_bytes,
+                  int32_t *cand_offsets, int64_t *d_total, void *stream);
+int pip_bin_fill(const int32_t *points, int64_t n_points,
+                 const int32_t *poly_offsets, const int32_t *verts, int32_t n_polys,
+                 void *workspace, size_t workspace_bytes,
+                 const int32_t *cand_offsets, int32_t *cand_ids, int64_t capacity,
+                 int32_t *d_overflow, void *stream);
+
+/*
+ * Tuning of pip_classify (the autotuner's hook; not in the paper).  edge_tile: edges staged
+ * in shared memory per pass (256..8192, multiple of 32); pts_per_thread: candidates each
+ * thread carries through the edge loop (1, 2 or 4); ctas_per_sm: resident CTAs per SM for
+ * the persistent grid (1..8).  0 keeps the current value.  Applies to later calls on every
+ * device; returns PIP_ERR_INVALID for an out-of-range value.
+ */
+int pip_set_tuning(int32_t edge_tile, int32_t pts_per_thread, int32_t ctas_per_sm);
+int pip_get_tuning(int32_t *edge_tile, int32_t *pts_per_thread, int32_t *ctas_per_sm);
+
+/* Statistics (device counters of the current device).  pip_get_stats copies them to the
+ * host with a synchronous copy: call it after the work of interest has completed. */
+int pip_get_stats(pip_stats *out);
+int pip_reset_stats(void);
+
+/*
+ * pip_validate -- opt-in device-side check of the data arrays of a pip_classify call.
+ * n_verts and n_cand_ids are the lengths of the verts and cand_ids allocations (in
+ * vertices and ids); the check reads poly_offsets, cand_offsets and at most n_cand_ids ids,
+ * never past them.  Writes *d_status (device int32): 0 if valid, else a bit mask:
+ *   1  poly_offsets negative or decreasing        2  cand_offsets decreasing or
+ *                                                    cand_offsets[0] != 0
+ *   4  a candidate id outside [0, n_points)       8  poly_offsets[n_polys] > n_verts
+ *  16  cand_offsets[n_polys] > n_cand_ids
+ * A call that passes makes pip_classify read only inside the given arrays.
+ */
+int pip_validate(const int32_t *points, int64_t n_points,
+                 const int32_t *poly_offsets, const int32_t *verts, int32_t n_polys,
+                 int64_t n_verts, const int32_t *cand_offsets, const int32_t *cand_ids,
+                 int64_t n_cand_ids, int32_t *d_status, void *stream);
+
+/* Human-readable name of a PIP_* status code. */
+const char *pip_status_str(int code);
+
+/* The last CUDA runtime error seen by the library on this thread (0 = none). */
+int pip_last_cuda_error(void);
+
+/* ABI version (major * 100 + minor). */
+int pip_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PIP_H */

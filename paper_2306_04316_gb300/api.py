@@ -1,0 +1,173 @@
+"""Python binding of libpip over torch tensors (device memory and streams only).
+
+Each ``pip_*`` function below has the name of the C entry point it forwards to and only
+marshals arguments: tensors become device pointers, the current torch CUDA stream becomes
+the ``stream`` argument.  All classification and binning work happens in libpip's kernels.
+Tensors are int32 and contiguous; ``points`` and ``verts`` are [n, 2] (x, y).  Output bits
+are returned in an int32 tensor holding the uint32 words of the C ABI.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import torch
+
+from . import _lib
+
+__all__ = ["pip_classify", "pip_classify_exact", "pip_bin_count", "pip_bin_fill", "bin_join",
+           "pip_set_tuning", "pip_get_tuning", "pip_get_stats", "pip_reset_stats", "pip_validate",
+           "out_words", "to_device"]
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _need(t, name, ndim=None):
+    if t is None:
+        return None
+    if not t.is_cuda or t.dtype != torch.int32 or not t.is_contiguous():
+        raise ValueError(f"{name} must be a contiguous int32 CUDA tensor")
+    if ndim == 2 and (t.dim() != 2 or t.shape[1] != 2):
+        raise ValueError(f"{name} must have shape [n, 2]")
+    return t
+
+
+def out_words(n_points: int, n_polys: int, n_cands=None) -> int:
+    """Words of out_bits: ceil(C / 32) in CSR mode, n_polys * ceil(n_points / 32) dense."""
+    if n_cands is None:
+        return n_polys * ((n_points + 31) // 32)
+    return (int(n_cands) + 31) // 32
+
+
+def to_device(workload, device="cuda"):
+    """Copy a ``workloads.Workload`` to int32 device tensors (a dict)."""
+    d = {k: torch.from_numpy(getattr(workload, k)).to(device)
+         for k in ("points", "poly_offsets", "verts")}
+    if workload.cand_offsets is not None:
+        d["cand_offsets"] = torch.from_numpy(workload.cand_offsets).to(device)
+        d["cand_ids"] = torch.from_numpy(workload.cand_ids).to(device)
+    return d
+
+
+def _classify(fn_name, points, poly_offsets, verts, cand_offsets, cand_ids, out, n_cands, stream):
+    lib = _lib.load()
+    _need(points, "points", 2)
+    _need(poly_offsets, "poly_offsets")
+    _need(verts, "verts", 2)
+    _need(cand_offsets, "cand_offsets")
+    _need(cand_ids, "cand_ids")
+    n_points = int(points.shape[0])
+    n_polys = int(poly_offsets.shape[0]) - 1
+    if out is None:
+        if cand_offsets is not None and n_cands is None:
+            n_cands = int(cand_offsets[-1].item()) if n_polys > 0 else 0
+        nw = out_words(n_points, n_polys, n_cands if cand_offsets is not None else None)
+        out = torch.empty(max(nw, 1), dtype=torch.int32, device=points.device)
+    _need(out, "out")
+    rc = getattr(lib, fn_name)(_ptr(points), n_points, _ptr(poly_offsets), _ptr(verts), n_polys,
+                               _ptr(cand_offsets), _ptr(cand_ids), _ptr(out), _stream(stream))
+    _lib.check(fn_name, rc)
+    return out
+
+
+def pip_classify(points, poly_offsets, verts, cand_offsets=None, cand_ids=None, out=None,
+                 n_cands=None, stream=None):
+    """FP32-filtered exact classification (``pip_classify``); returns out_bits."""
+    return _classify("pip_classify", points, poly_offsets, verts, cand_offsets, cand_ids, out,
+                     n_cands, stream)
+
+
+def pip_classify_exact(points, poly_offsets, verts, cand_offsets=None, cand_ids=None, out=None,
+                       n_cands=None, stream=None):
+    """Plain exact integer classification (``pip_classify_exact``); returns out_bits."""
+    return _classify("pip_classify_exact", points, poly_offsets, verts, cand_offsets, cand_ids,
+                     out, n_cands, stream)
+
+
+def bin_workspace(n_points: int, n_polys: int, device="cuda"):
+    lib = _lib.load()
+    nbytes = int(lib.pip_bin_workspace_bytes(n_points, n_polys))
+    return torch.empty(nbytes, dtype=torch.uint8, device=device)
+
+
+def pip_bin_count(points, poly_offsets, verts, cell_size=0, workspace=None, cand_offsets=None,
+                  d_total=None, stream=None):
+    """Grid binning, counting pass: returns (cand_offsets, d_total, workspace)."""
+    lib = _lib.load()
+    _need(points, "points", 2)
+    _need(poly_offsets, "poly_offsets")
+    _need(verts, "verts", 2)
+    n_points = int(points.shape[0])
+    n_polys = int(poly_offsets.shape[0]) - 1
+    if workspace is None:
+        workspace = bin_workspace(n_points, n_polys, points.device)
+    if cand_offsets is None:
+        cand_offsets = torch.empty(n_polys + 1, dtype=torch.int32, device=points.device)
+    if d_total is None:
+        d_total = torch.empty(1, dtype=torch.int64, device=points.device)
+    rc = lib.pip_bin_count(_ptr(points), n_points, _ptr(poly_offsets), _ptr(verts), n_polys,
+                           int(cell_size), _ptr(workspace), workspace.numel(), _ptr(cand_offsets),
+                           _ptr(d_total), _stream(stream))
+    _lib.check("pip_bin_count", rc)
+    return cand_offsets, d_total, workspace
+
+
+def pip_bin_fill(points, poly_offsets, verts, workspace, cand_offsets, cand_ids, d_overflow=None,
+                 stream=None):
+    """Grid binning, fill pass: writes cand_ids (capacity = its length); returns cand_ids."""
+    lib = _lib.load()
+    n_points = int(points.shape[0])
+    n_polys = int(poly_offsets.shape[0]) - 1
+    rc = lib.pip_bin_fill(_ptr(points), n_points, _ptr(poly_offsets), _ptr(verts), n_polys,
+                          _ptr(workspace), workspace.numel(), _ptr(cand_offsets), _ptr(cand_ids),
+                          int(cand_ids.numel()), _ptr(d_overflow), _stream(stream))
+    _lib.check("pip_bin_fill", rc)
+    return cand_ids
+
+
+def bin_join(points, poly_offsets, verts, cell_size=0, stream=None):
+    """Both binning passes with one host read of the candidate total in between."""
+    co, tot, ws = pip_bin_count(points, poly_offsets, verts, cell_size, stream=stream)
+    total = int(tot.item())
+    ids = torch.empty(max(total, 1), dtype=torch.int32, device=points.device)
+    pip_bin_fill(points, poly_offsets, verts, ws, co, ids[:total] if total else ids[:0], stream=stream)
+    return co, ids[:total]
+
+
+def pip_set_tuning(edge_tile=0, pts_per_thread=0, ctas_per_sm=0):
+    _lib.check("pip_set_tuning", _lib.load().pip_set_tuning(edge_tile, pts_per_thread, ctas_per_sm))
+
+
+def pip_get_tuning():
+    a, b, c = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+    _lib.check("pip_get_tuning", _lib.load().pip_get_tuning(ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
+    return a.value, b.value, c.value
+
+
+def pip_get_stats() -> dict:
+    s = _lib.PipStats()
+    _lib.check("pip_get_stats", _lib.load().pip_get_stats(ctypes.byref(s)))
+    return {f: int(getattr(s, f)) for f, _ in _lib.PipStats._fields_}
+
+
+def pip_reset_stats():
+    _lib.check("pip_reset_stats", _lib.load().pip_reset_stats())
+
+
+def pip_validate(points, poly_offsets, verts, cand_offsets=None, cand_ids=None, stream=None) -> int:
+    """Device-side data check; returns the status mask (0 = valid).  Synchronises."""
+    lib = _lib.load()
+    st = torch.zeros(1, dtype=torch.int32, device=points.device)
+    n_ids = int(cand_ids.numel()) if cand_ids is not None else 0
+    rc = lib.pip_validate(_ptr(points), int(points.shape[0]), _ptr(poly_offsets), _ptr(verts),
+                          int(poly_offsets.shape[0]) - 1, int(verts.shape[0]), _ptr(cand_offsets),
+                          _ptr(cand_ids), n_ids, _ptr(st), _stream(stream))
+    _lib.check("pip_validate", rc)
+    return int(st.item())

@@ -1,0 +1,339 @@
+// C ABI of libpip (declared in include/pip.h): argument checks, the per-device
+// workspace, tuning state, statistics and the opt-in device-side validation.
+#include <atomic>
+#include <climits>
+#include <cstring>
+#include <mutex>
+
+#include "pip.h"
+#include "pip_device.cuh"
+#include "pip_launch.h"
+
+using namespace pipdev;
+
+namespace {
+
+constexpr int MAX_DEVICES = 64;
+
+struct DeviceState {
+    unsigned long long *stats = nullptr;   // ST_COUNT counters
+    int n_sm = 0;
+};
+
+std::mutex g_mu;
+DeviceState g_dev[MAX_DEVICES];
+std::atomic<int> g_edge_tile{2048};
+std::atomic<int> g_ppt{2};
+std::atomic<int> g_ctas{3};
+thread_local int g_last_cuda = 0;
+
+int cuda_fail(cudaError_t e)
+{
+    g_last_cuda = (int)e;
+    return PIP_ERR_CUDA;
+}
+
+bool capturing(cudaStream_t s)
+{
+    cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &st) != cudaSuccess) return false;
+    return st != cudaStreamCaptureStatusNone;
+}
+
+// Per-device workspace (statistics counters), created on first use outside capture.
+int device_state(cudaStream_t stream, DeviceState **out)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e);
+    if (dev < 0 || dev >= MAX_DEVICES) return PIP_ERR_WORKSPACE;
+    std::lock_guard<std::mutex> lock(g_mu);
+    DeviceState &s = g_dev[dev];
+    if (!s.stats) {
+        if (capturing(stream)) return PIP_ERR_WORKSPACE;
+        int n_sm = 0;
+        e = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+        if (e != cudaSuccess) return cuda_fail(e);
+        unsigned long long *p = nullptr;
+        e = cudaMalloc(&p, ST_COUNT * sizeof(unsigned long long));
+        if (e != cudaSuccess) return cuda_fail(e);
+        e = cudaMemset(p, 0, ST_COUNT * sizeof(unsigned long long));
+        if (e != cudaSuccess) { cudaFree(p); return cuda_fail(e); }
+        s.n_sm = n_sm;
+        s.stats = p;
+    }
+    *out = &s;
+    return PIP_OK;
+}
+
+bool misaligned(const void *p, size_t a) { return p && (reinterpret_cast<uintptr_t>(p) % a) != 0; }
+
+int check_classify(const int32_t *points, int64_t n_points, const int32_t *poly_offsets,
+                   const int32_t *verts, int32_t n_polys, const int32_t *cand_offsets,
+                   const int32_t *cand_ids, const void *out)
+{
+    if (n_points < 0 || n_polys < 0) return PIP_ERR_SIZE;
+    if ((cand_offsets == nullptr) != (cand_ids == nullptr)) return PIP_ERR_NULL;
+    if (n_polys > 0 && (!poly_offsets || !verts || !out)) return PIP_ERR_NULL;
+    if (n_points > 0 && !points) return PIP_ERR_NULL;
+    if (misaligned(points, 8) || misaligned(verts, 8)) return PIP_ERR_ALIGN;
+    if (misaligned(poly_offsets, 4) || misaligned(cand_offsets, 4) || misaligned(cand_ids, 4) ||
+        misaligned(out, 4))
+        return PIP_ERR_ALIGN;
+    if (n_points > (int64_t)INT_MAX) return PIP_ERR_TOO_LARGE;   // ids are int32
+    return PIP_OK;
+}
+
+ClassifyArgs make_args(const int32_t *points, int64_t n_points, const int32_t *poly_offsets,
+                       const int32_t *verts, int32_t n_polys, const int32_t *cand_offsets,
+                       const int32_t *cand_ids, uint32_t *out_bits, unsigned long long *stats)
+{
+    ClassifyArgs a;
+    a.points = reinterpret_cast<const int2 *>(points);
+    a.n_points = n_points;
+    a.poly_offsets = poly_offsets;
+    a.verts = reinterpret_cast<const int2 *>(verts);
+    a.n_polys = n_polys;
+    a.cand_offsets = cand_offsets;
+    a.cand_ids = cand_ids;
+    a.out_bits = out_bits;
+    a.words_per_poly = (n_points + 31) / 32;
+    a.stats = stats;
+    return a;
+}
+
+}  // namespace
+
+extern "C" {
+
+int pip_classify(const int32_t *points, int64_t n_points, const int32_t *poly_offsets,
+                 const int32_t *verts, int32_t n_polys, const int32_t *cand_offsets,
+                 const int32_t *cand_ids, uint32_t *out_bits, void *stream)
+{
+    int rc = check_classify(points, n_points, poly_offsets, verts, n_polys, cand_offsets, cand_ids, out_bits);
+    if (rc != PIP_OK) return rc;
+    if (n_polys == 0) return PIP_OK;
+    const bool dense = cand_offsets == nullptr;
+    const long long total_bits = dense ? (long long)n_polys * 32 * ((n_points + 31) / 32) : 0;
+    if (dense && total_bits == 0) return PIP_OK;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    DeviceState *ds = nullptr;
+    rc = device_state(s, &ds);
+    if (rc != PIP_OK) return rc;
+    ClassifyArgs a = make_args(points, n_points, poly_offsets, verts, n_polys, cand_offsets, cand_ids,
+                               out_bits, ds->stats);
+    Tuning t{g_edge_tile.load(), g_ppt.load(), g_ctas.load()};
+    int e = launch_filtered(a, total_bits, t, ds->n_sm, s);
+    return e == 0 ? PIP_OK : cuda_fail((cudaError_t)e);
+}
+
+int pip_classify_exact(const int32_t *points, int64_t n_points, const int32_t *poly_offsets,
+                       const int32_t *verts, int32_t n_polys, const int32_t *cand_offsets,
+                       const int32_t *cand_ids, uint32_t *out_bits, void *stream)
+{
+    int rc = check_classify(points, n_points, poly_offsets, verts, n_polys, cand_offsets, cand_ids, out_bits);
+    if (rc != PIP_OK) return rc;
+    if (n_polys == 0) return PIP_OK;
+    const bool dense = cand_offsets == nullptr;
+    const long long total_bits = dense ? (long long)n_polys * 32 * ((n_points + 31) / 32) : 0;
+    if (dense && total_bits == 0) return PIP_OK;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    DeviceState *ds = nullptr;
+    rc = device_state(s, &ds);
+    if (rc != PIP_OK) return rc;
+    ClassifyArgs a = make_args(points, n_points, poly_offsets, verts, n_polys, cand_offsets, cand_ids,
+                               out_bits, ds->stats);
+    long long grid = (long long)ds->n_sm * 8;
+    if (dense) grid = std::min(grid, (total_bits / 32 + 7) / 8);
+    if (grid < 1) grid = 1;
+    int e = launch_exact(a, total_bits, (int)grid, s);
+    return e == 0 ? PIP_OK : cuda_fail((cudaError_t)e);
+}
+
+int pip_set_tuning(int32_t edge_tile, int32_t pts_per_thread, int32_t ctas_per_sm)
+{
+    if (edge_tile != 0 && (edge_tile < 256 || edge_tile > 6144 || edge_tile % 32 != 0)) return PIP_ERR_INVALID;
+    if (pts_per_thread != 0 && pts_per_thread != 1 && pts_per_thread != 2 && pts_per_thread != 4)
+        return PIP_ERR_INVALID;
+    if (ctas_per_sm != 0 && (ctas_per_sm < 1 || ctas_per_sm > 8)) return PIP_ERR_INVALID;
+    if (edge_tile) g_edge_tile.store(edge_tile);
+    if (pts_per_thread) g_ppt.store(pts_per_thread);
+    if (ctas_per_sm) g_ctas.store(ctas_per_sm);
+    return PIP_OK;
+}
+
+int pip_get_tuning(int32_t *edge_tile, int32_t *pts_per_thread, int32_t *ctas_per_sm)
+{
+    if (!edge_tile || !pts_per_thread || !ctas_per_sm) return PIP_ERR_NULL;
+    *edge_tile = g_edge_tile.load();
+    *pts_per_thread = g_ppt.load();
+    *ctas_per_sm = g_ctas.load();
+    return PIP_OK;
+}
+
+int pip_get_stats(pip_stats *out)
+{
+    if (!out) return PIP_ERR_NULL;
+    DeviceState *ds = nullptr;
+    int rc = device_state(nullptr, &ds);
+    if (rc != PIP_OK) return rc;
+    unsigned long long h[ST_COUNT];
+    cudaError_t e = cudaMemcpy(h, ds->stats, sizeof h, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e);
+    out->candidates = h[ST_CANDIDATES];
+    out->bbox_rejects = h[ST_BBOX_REJECTS];
+    out->fallback_points = h[ST_FALLBACK_POINTS];
+    out->fallback_edges = h[ST_FALLBACK_EDGES];
+    out->exact_candidates = h[ST_EXACT_CANDIDATES];
+    return PIP_OK;
+}
+
+int pip_reset_stats(void)
+{
+    DeviceState *ds = nullptr;
+    int rc = device_state(nullptr, &ds);
+    if (rc != PIP_OK) return rc;
+    cudaError_t e = cudaMemset(ds->stats, 0, ST_COUNT * sizeof(unsigned long long));
+    return e == cudaSuccess ? PIP_OK : cuda_fail(e);
+}
+
+int pip_validate(const int32_t *points, int64_t n_points, const int32_t *poly_offsets,
+                 const int32_t *verts, int32_t n_polys, int64_t n_verts, const int32_t *cand_offsets,
+                 const int32_t *cand_ids, int64_t n_cand_ids, int32_t *d_status, void *stream)
+{
+    if (!d_status) return PIP_ERR_NULL;
+    if (n_verts < 0 || n_cand_ids < 0) return PIP_ERR_SIZE;
+    int rc = check_classify(points, n_points, poly_offsets, verts, n_polys, cand_offsets, cand_ids,
+                            d_status);
+    if (rc != PIP_OK) return rc;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    DeviceState *ds = nullptr;
+    rc = device_state(s, &ds);
+    if (rc != PIP_OK) return rc;
+    cudaError_t e = cudaMemsetAsync(d_status, 0, sizeof(int32_t), s);
+    if (e != cudaSuccess) return cuda_fail(e);
+    if (n_polys == 0) return PIP_OK;
+    ClassifyArgs a = make_args(points, n_points, poly_offsets, verts, n_polys, cand_offsets, cand_ids,
+                               nullptr, nullptr);
+    int err = launch_validate(a, n_verts, n_cand_ids, d_status, ds->n_sm * 4, s);
+    return err == 0 ? PIP_OK : cuda_fail((cudaError_t)err);
+}
+
+size_t pip_bin_workspace_bytes(int64_t n_points, int32_t n_polys)
+{
+    if (n_points < 0 || n_polys < 0) return 0;
+    return bin_workspace_bytes(n_points, n_polys);
+}
+
+int pip_bin_count(const int32_t *points, int64_t n_points, const int32_t *poly_offsets,
+                  const int32_t *verts, int32_t n_polys, int32_t cell_size, void *workspace,
+                  size_t workspace_bytes, int32_t *cand_offsets, int64_t *d_total, void *stream)
+{
+    if (n_points < 0 || n_polys < 0 || cell_size < 0) return PIP_ERR_SIZE;
+    if (n_points > (int64_t)INT_MAX) return PIP_ERR_TOO_LARGE;
+    if (!cand_offsets || !d_total || !workspace) return PIP_ERR_NULL;
+    if (n_polys > 0 && (!poly_offsets || !verts)) return PIP_ERR_NULL;
+    if (n_points > 0 && !points) return PIP_ERR_NULL;
+    if (misaligned(points, 8) || misaligned(verts, 8) || misaligned(workspace, 16) ||
+        misaligned(d_total, 8) || misaligned(cand_offsets, 4) || misaligned(poly_offsets, 4))
+        return PIP_ERR_ALIGN;
+    if (workspace_bytes < bin_workspace_bytes(n_points, n_polys)) return PIP_ERR_WORKSPACE;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    DeviceState *ds = nullptr;
+    int rc = device_state(s, &ds);
+    if (rc != PIP_OK) return rc;
+    int e = launch_bin_count(reinterpret_cast<const int2 *>(points), n_points, poly_offsets,
+                             reinterpret_cast<const int2 *>(verts), n_polys, cell_size, workspace,
+                             workspace_bytes, cand_offsets, reinterpret_cast<long long *>(d_total),
+                             ds->n_sm, s);
+    return e == 0 ? PIP_OK : cuda_fail((cudaError_t)e);
+}
+
+int pip_bin_fill(const int32_t *points, int64_t n_points, const int32_t *poly_offsets,
+                 const int32_t *verts, int32_t n_polys, void *workspace, size_t workspace_bytes,
+                 const int32_t *cand_offsets, int32_t *cand_ids, int64_t capacity,
+                 int32_t *d_overflow, void *stream)
+{
+    if (n_points < 0 || n_polys < 0 || capacity < 0) return PIP_ERR_SIZE;
+    if (n_points > (int64_t)INT_MAX) return PIP_ERR_TOO_LARGE;
+    if (!cand_offsets || !workspace || (capacity > 0 && !cand_ids)) return PIP_ERR_NULL;
+    if (n_polys > 0 && (!poly_offsets || !verts)) return PIP_ERR_NULL;
+    if (n_points > 0 && !points) return PIP_ERR_NULL;
+    if (misaligned(points, 8) || misaligned(verts, 8) || misaligned(workspace, 16) ||
+        misaligned(cand_ids, 4) || misaligned(cand_offsets, 4) || misaligned(poly_offsets, 4) ||
+        misaligned(d_overflow, 4))
+        return PIP_ERR_ALIGN;
+    if (workspace_bytes < bin_workspace_bytes(n_points, n_polys)) return PIP_ERR_WORKSPACE;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    DeviceState *ds = nullptr;
+    int rc = device_state(s, &ds);
+    if (rc != PIP_OK) return rc;
+    int e = launch_bin_fill(reinterpret_cast<const int2 *>(points), n_points, poly_offsets,
+                            reinterpret_cast<const int2 *>(verts), n_polys, workspace, workspace_bytes,
+                            cand_offsets, cand_ids, capacity, d_overflow, ds->n_sm, s);
+    return e == 0 ? PIP_OK : cuda_fail((cudaError_t)e);
+}
+
+const char *pip_status_str(int code)
+{
+    switch (code) {
+        case PIP_OK: return "PIP_OK";
+        case PIP_ERR_NULL: return "PIP_ERR_NULL: a required pointer is NULL";
+        case PIP_ERR_SIZE: return "PIP_ERR_SIZE: negative size or capacity too small";
+        case PIP_ERR_ALIGN: return "PIP_ERR_ALIGN: misaligned pointer";
+        case PIP_ERR_TOO_LARGE: return "PIP_ERR_TOO_LARGE: count beyond int32 addressing";
+        case PIP_ERR_WORKSPACE: return "PIP_ERR_WORKSPACE: workspace missing or too small";
+        case PIP_ERR_CUDA: return "PIP_ERR_CUDA: CUDA runtime error";
+        case PIP_ERR_INVALID: return "PIP_ERR_INVALID: invalid value";
+        default: return "unknown status";
+    }
+}
+
+int pip_last_cuda_error(void) { return g_last_cuda; }
+
+int pip_version(void) { return 100; }
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------------------------
+// opt-in device-side validation of the data arrays
+// ---------------------------------------------------------------------------------------------
+namespace pipdev {
+
+__global__ void k_validate(ClassifyArgs a, long long n_verts, long long n_cand_ids, int *status)
+{
+    const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long nthr = (long long)gridDim.x * blockDim.x;
+    int bad = 0;
+    for (long long k = tid; k < a.n_polys; k += nthr) {
+        const int p0 = a.poly_offsets[k], p1 = a.poly_offsets[k + 1];
+        if (p0 < 0 || p1 < p0) bad |= 1;
+        if (a.cand_offsets) {
+            const int c0 = a.cand_offsets[k], c1 = a.cand_offsets[k + 1];
+            if (c1 < c0 || c0 < 0) bad |= 2;
+        }
+    }
+    if (tid == 0 && (long long)a.poly_offsets[a.n_polys] > n_verts) bad |= 8;
+    if (a.cand_offsets) {
+        if (tid == 0 && a.cand_offsets[0] != 0) bad |= 2;
+        long long C = a.cand_offsets[a.n_polys];
+        if (C > n_cand_ids) {
+            if (tid == 0) bad |= 16;
+            C = n_cand_ids;
+        }
+        for (long long c = tid; c < C; c += nthr) {
+            const int id = a.cand_ids[c];
+            if (id < 0 || (long long)id >= a.n_points) bad |= 4;
+        }
+    }
+    if (bad) atomicOr(status, bad);
+}
+
+int launch_validate(const ClassifyArgs &a, long long n_verts, long long n_cand_ids, int *d_status, int grid,
+                    cudaStream_t stream)
+{
+    k_validate<<<grid, 256, 0, stream>>>(a, n_verts, n_cand_ids, d_status);
+    return (int)cudaGetLastError();
+}
+
+}  // namespace pipdev

@@ -1,0 +1,99 @@
+// Device helpers shared by the CUDA kernels of libpip (sm_103a).
+//
+// Method section, seven-step algorithm with Constraint 1: for a query point p and the
+// edge R_i -> R_j (j = i + 1, cyclic) the ray d = (1, 0) from p crosses the edge when
+// f(R_i) = y_i - p_y and f(R_j) = y_j - p_y lie on opposite sides of the ray, and the
+// crossing lies to the right of p when the side test (p - R_i) . n, with the edge normal
+// n = (d_y, -d_x) oriented so that n_x >= 0, is negative.  With det = (x_i - p_x) d_y -
+// (y_i - p_y) d_x this is sign(d_y) * det > 0.  Half-open reading: a vertex with
+// y = p_y lies below the ray, and a crossing exactly at p does not count.
+#pragma once
+
+#include <cstdint>
+#include <climits>
+#include <cuda_runtime.h>
+
+namespace pipdev {
+
+constexpr unsigned FULL = 0xffffffffu;
+
+// Device-side statistics counters (indices into the workspace array).
+enum StatIdx {
+    ST_CANDIDATES = 0,
+    ST_BBOX_REJECTS = 1,
+    ST_FALLBACK_POINTS = 2,
+    ST_FALLBACK_EDGES = 3,
+    ST_EXACT_CANDIDATES = 4,
+    ST_COUNT = 8
+};
+
+struct ClassifyArgs {
+    const int2 *points;
+    long long n_points;
+    const int32_t *poly_offsets;
+    const int2 *verts;
+    int n_polys;
+    const int32_t *cand_offsets;   // nullptr => dense mode
+    const int32_t *cand_ids;
+    uint32_t *out_bits;
+    long long words_per_poly;      // dense mode: W = ceil(n_points / 32)
+    unsigned long long *stats;     // device counters (may be nullptr)
+};
+
+// |v| < 2^31, so that products of two such values fit in 62 bits.
+__device__ __forceinline__ bool fits31(long long v)
+{
+    return (unsigned long long)(v + 0x7fffffffLL) <= 0xfffffffeULL;
+}
+
+// Exact side test of a straddling edge (x_i, y_i) -> (x_j, y_j): 1 when the crossing of
+// the ray from (px, py) lies strictly to its right.  int64 products when every difference
+// is below 2^31 in magnitude, 128-bit products otherwise (full int32 range).
+__device__ __forceinline__ int exact_edge_counts(int px, int py, int xi, int yi, int xj, int yj)
+{
+    long long ax = (long long)xi - px, ay = (long long)yi - py;
+    long long dx = (long long)xj - xi, dy = (long long)yj - yi;
+    int sgn;
+    if (fits31(ax) & fits31(ay) & fits31(dx) & fits31(dy)) {
+        long long det = ax * dy - ay * dx;
+        sgn = (det > 0) - (det < 0);
+    } else {
+        __int128 det = (__int128)ax * dy - (__int128)ay * dx;
+        sgn = (det > 0) - (det < 0);
+    }
+    return dy > 0 ? (sgn > 0) : (sgn < 0);
+}
+
+// Largest k in [0, n_polys) with co[k] <= c0, found by a warp with 32-way probes
+// (log32(n_polys) rounds of one load per lane).  Returns -1 when co[0] > c0.  Every
+// lane of the warp must call it with the same arguments.
+__device__ __forceinline__ int warp_owner_search(const int32_t *__restrict__ co, int n_polys,
+                                                 long long c0, int lane)
+{
+    if (n_polys <= 0 || (long long)__ldg(co) > c0) return -1;
+    int lo = 0, hi = n_polys;
+    while (hi - lo > 1) {
+        int step = (hi - lo + 31) >> 5;
+        long long probe = (long long)lo + (long long)lane * step;
+        bool ok = probe < hi && (long long)__ldg(co + probe) <= c0;
+        unsigned mask = __ballot_sync(FULL, ok);
+        int j = 31 - __clz(mask);          // bit 0 is set: co[lo] <= c0
+        lo = lo + j * step;
+        hi = min(lo + step, hi);
+    }
+    return lo;
+}
+
+// First index i in [0, n) with a[i] > v (n if none); a non-decreasing.
+template <typename T, typename V>
+__device__ __forceinline__ int upper_bound_dev(const T *a, int n, V v)
+{
+    int lo = 0, hi = n;
+    while (lo < hi) {
+        int mid = (lo + hi) >> 1;
+        if ((V)a[mid] <= v) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+
+}  // namespace pipdev

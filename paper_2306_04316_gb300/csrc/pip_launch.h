@@ -1,0 +1,36 @@
+// Internal launch helpers of libpip (host side; not part of the public C ABI).
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace pipdev {
+
+struct ClassifyArgs;
+
+// Tuned shape of the filtered kernel.
+struct Tuning {
+    int edge_tile;       // edges staged in shared memory per pass
+    int pts_per_thread;  // candidates carried by each thread (1, 2, 4)
+    int ctas_per_sm;     // resident CTAs per SM of the persistent grid
+};
+
+int launch_exact(const ClassifyArgs &a, long long total_bits, int grid, cudaStream_t stream);
+int launch_filtered(const ClassifyArgs &a, long long total_bits, const Tuning &t, int n_sm,
+                    cudaStream_t stream);
+size_t filtered_smem_bytes(int edge_tile);
+int launch_validate(const ClassifyArgs &a, long long n_verts, long long n_cand_ids, int *d_status, int grid,
+                    cudaStream_t stream);
+
+// binning
+size_t bin_workspace_bytes(long long n_points, int n_polys);
+int launch_bin_count(const int2 *points, long long n_points, const int32_t *poly_offsets,
+                     const int2 *verts, int n_polys, int cell_size, void *ws, size_t ws_bytes,
+                     int32_t *cand_offsets, long long *d_total, int n_sm, cudaStream_t stream);
+int launch_bin_fill(const int2 *points, long long n_points, const int32_t *poly_offsets,
+                    const int2 *verts, int n_polys, void *ws, size_t ws_bytes,
+                    const int32_t *cand_offsets, int32_t *cand_ids, long long capacity,
+                    int32_t *d_overflow, int n_sm, cudaStream_t stream);
+
+}  // namespace pipdev

@@ -98,6 +98,17 @@ class Workload:
         C = self.n_bits
         return 8 * V + 8 * (P + 1) + 12 * C + self.n_words * 4
 
+    def prefix(self, n_polys: int) -> "Workload":
+        """The first n_polys polygons with their candidates (CSR mode; points kept whole)."""
+        n = max(0, min(int(n_polys), self.n_polys))
+        po = self.poly_offsets[:n + 1]
+        v = self.verts[:int(po[-1])] if n else self.verts[:0]
+        if self.dense:
+            return dataclasses.replace(self, poly_offsets=po, verts=v)
+        co = self.cand_offsets[:n + 1]
+        return dataclasses.replace(self, poly_offsets=po, verts=v, cand_offsets=co,
+                                   cand_ids=self.cand_ids[:int(co[-1])] if n else self.cand_ids[:0])
+
     def with_csr(self, cand_offsets, cand_ids, name=None):
         return dataclasses.replace(self, name=name or self.name,
                                    cand_offsets=np.ascontiguousarray(cand_offsets, dtype=np.int32),

@@ -1,0 +1,101 @@
+"""Host-side checks of the C ABI (no GPU needed): the library builds for sm_103a, loads,
+exports every function declared in include/pip.h, and rejects bad arguments before it
+touches a device."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2306_04316_gb300 import build, _lib
+    build.build_library()
+    return _lib.load()
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "pip.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    names = re.findall(r"^\s*(?:const\s+)?[\w]+\s*\*?\s*(pip_\w+)\s*\(", src, flags=re.M)
+    return sorted(set(names))
+
+
+def test_header_declares_entry_points():
+    names = declared_functions()
+    for must in ("pip_classify", "pip_classify_exact", "pip_bin_count", "pip_bin_fill",
+                 "pip_set_tuning", "pip_get_stats", "pip_validate", "pip_status_str"):
+        assert must in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, f"not exported: {missing}"
+
+
+def test_binding_covers_every_symbol(lib):
+    from paper_2306_04316_gb300 import _lib
+    assert sorted(_lib._SIGS) == declared_functions()
+
+
+def test_status_strings(lib):
+    for code in range(-7, 1):
+        assert lib.pip_status_str(code).startswith(b"PIP_")
+    assert lib.pip_version() >= 100
+
+
+def test_argument_checks_return_before_any_device_call(lib):
+    from paper_2306_04316_gb300 import _lib
+    P = ctypes.c_void_p
+    a8 = P(0x1000)          # never dereferenced: every call below fails its host checks
+    odd = P(0x1004)
+    # negative sizes
+    assert lib.pip_classify(a8, -1, a8, a8, 1, None, None, a8, None) == _lib.PIP_ERR_SIZE
+    assert lib.pip_classify(a8, 4, a8, a8, -2, None, None, a8, None) == _lib.PIP_ERR_SIZE
+    # only one half of the CSR
+    assert lib.pip_classify(a8, 4, a8, a8, 1, a8, None, a8, None) == _lib.PIP_ERR_NULL
+    assert lib.pip_classify_exact(a8, 4, a8, a8, 1, None, a8, a8, None) == _lib.PIP_ERR_NULL
+    # missing arrays
+    assert lib.pip_classify(None, 4, a8, a8, 1, None, None, a8, None) == _lib.PIP_ERR_NULL
+    assert lib.pip_classify(a8, 4, None, a8, 1, None, None, a8, None) == _lib.PIP_ERR_NULL
+    assert lib.pip_classify(a8, 4, a8, a8, 1, None, None, None, None) == _lib.PIP_ERR_NULL
+    # int2 arrays must be 8-byte aligned
+    assert lib.pip_classify(odd, 4, a8, a8, 1, None, None, a8, None) == _lib.PIP_ERR_ALIGN
+    assert lib.pip_classify(a8, 4, a8, odd, 1, None, None, a8, None) == _lib.PIP_ERR_ALIGN
+    assert lib.pip_classify(a8, 4, P(0x1002), a8, 1, None, None, a8, None) == _lib.PIP_ERR_ALIGN
+    # ids are int32
+    assert lib.pip_classify(a8, 2**31, a8, a8, 1, None, None, a8, None) == _lib.PIP_ERR_TOO_LARGE
+    # nothing to do: no polygons
+    assert lib.pip_classify(a8, 4, a8, a8, 0, None, None, a8, None) == _lib.PIP_OK
+    # binning
+    assert lib.pip_bin_count(a8, 4, a8, a8, 1, -1, a8, 1 << 30, a8, a8, None) == _lib.PIP_ERR_SIZE
+    assert lib.pip_bin_count(a8, 4, a8, a8, 1, 0, a8, 16, a8, a8, None) == _lib.PIP_ERR_WORKSPACE
+    assert lib.pip_bin_fill(a8, 4, a8, a8, 1, a8, 1 << 30, a8, a8, -1, None, None) == _lib.PIP_ERR_SIZE
+    # validate
+    assert lib.pip_validate(a8, 4, a8, a8, 1, 4, None, None, 0, None, None) == _lib.PIP_ERR_NULL
+    assert lib.pip_validate(a8, 4, a8, a8, 1, -4, None, None, 0, a8, None) == _lib.PIP_ERR_SIZE
+
+
+def test_tuning_validation(lib):
+    from paper_2306_04316_gb300 import _lib
+    t = [ctypes.c_int32() for _ in range(3)]
+    assert lib.pip_get_tuning(*[ctypes.byref(x) for x in t]) == 0
+    before = [x.value for x in t]
+    assert lib.pip_set_tuning(100, 0, 0) == _lib.PIP_ERR_INVALID      # below 256
+    assert lib.pip_set_tuning(2050, 0, 0) == _lib.PIP_ERR_INVALID     # not a multiple of 32
+    assert lib.pip_set_tuning(0, 3, 0) == _lib.PIP_ERR_INVALID
+    assert lib.pip_set_tuning(0, 0, 9) == _lib.PIP_ERR_INVALID
+    assert lib.pip_set_tuning(1024, 4, 2) == 0
+    assert lib.pip_get_tuning(*[ctypes.byref(x) for x in t]) == 0
+    assert [x.value for x in t] == [1024, 4, 2]
+    assert lib.pip_set_tuning(*before) == 0
+
+
+def test_bin_workspace_size_grows(lib):
+    a = lib.pip_bin_workspace_bytes(1000, 10)
+    b = lib.pip_bin_workspace_bytes(10_000_000, 100_000)
+    assert 0 < a < b
+    assert b >= 10_000_000 * (4 * 4 + 8)

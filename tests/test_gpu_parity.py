@@ -1,0 +1,225 @@
+"""GPU parity: both kernels through the C ABI against the CPU oracle, bit for bit.
+
+Every case below compares all output bits (0 mismatches required) unless it says
+"sampled": at the full sizes whose oracle run would take minutes, a seeded sample of
+candidates is checked one by one with the oracle's sampled entry point.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2306_04316_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def api():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2306_04316_gb300 import api as _api, build
+    build.build_library()
+    oracle.build()
+    return _api
+
+
+def gpu_bits(api, w, exact=False, dev="cuda"):
+    d = api.to_device(w, dev)
+    fn = api.pip_classify_exact if exact else api.pip_classify
+    out = fn(d["points"], d["poly_offsets"], d["verts"], d.get("cand_offsets"), d.get("cand_ids"),
+             n_cands=None if w.dense else w.n_bits)
+    torch.cuda.synchronize()
+    return out.cpu().numpy().view(np.uint32)[:w.n_words]
+
+
+def assert_same(got, want, n_bits, what):
+    if not np.array_equal(got, want):
+        g, o = oracle.unpack_bits(got, n_bits), oracle.unpack_bits(want, n_bits)
+        bad = np.nonzero(g != o)[0]
+        raise AssertionError(f"{what}: {len(bad)} mismatched bits of {n_bits}; first {bad[:10].tolist()}")
+
+
+def check_full(api, w, what=""):
+    want = oracle.classify(w.points, w.poly_offsets, w.verts, w.cand_offsets, w.cand_ids)
+    for exact in (False, True):
+        got = gpu_bits(api, w, exact)
+        assert_same(got, want, w.n_bits, f"{w.name} {what} {'exact' if exact else 'filtered'}")
+
+
+def make(name, polys, points, csr=None):
+    """Workload from python lists: polys = list of vertex lists, csr = list of id lists."""
+    po = np.zeros(len(polys) + 1, dtype=np.int64)
+    po[1:] = np.cumsum([len(p) for p in polys])
+    verts = np.array([v for p in polys for v in p], dtype=np.int64).reshape(-1, 2).astype(np.int32)
+    pts = np.array(points, dtype=np.int64).reshape(-1, 2).astype(np.int32)
+    w = W.Workload(name, pts, po.astype(np.int32), verts)
+    if csr is not None:
+        co = np.zeros(len(csr) + 1, dtype=np.int64)
+        co[1:] = np.cumsum([len(c) for c in csr])
+        ids = np.array([i for c in csr for i in c], dtype=np.int32)
+        w = w.with_csr(co.astype(np.int32), ids)
+    return w
+
+
+# ------------------------------------------------------------------------------------------
+# small and degenerate cases
+# ------------------------------------------------------------------------------------------
+
+def test_golden_cases(api):
+    import json, os
+    g = os.path.join(os.path.dirname(__file__), "golden")
+    d = json.load(open(os.path.join(g, "diamond.json")))
+    s = json.load(open(os.path.join(g, "square.json")))
+    w = make("diamond", [d["verts"]], [d["point"]])
+    for exact in (False, True):
+        assert oracle.unpack_bits(gpu_bits(api, w, exact), 1)[0] == d["inside_half_open"]
+    w = make("square", [s["verts"]], [c[0] for c in s["cases"]])
+    want = np.array([c[1] for c in s["cases"]])
+    for exact in (False, True):
+        assert (oracle.unpack_bits(gpu_bits(api, w, exact), len(want)) == want).all()
+
+
+@pytest.mark.parametrize("n_points", [0, 1, 31, 32, 33, 1000])
+def test_point_counts_dense(api, n_points):
+    rng = np.random.default_rng(n_points)
+    polys = [[tuple(map(int, rng.integers(0, 40, 2))) for _ in range(int(rng.integers(3, 12)))] for _ in range(5)]
+    pts = rng.integers(-2, 42, size=(n_points, 2))
+    w = make("dense-small", polys, pts)
+    if w.n_words == 0:
+        return
+    check_full(api, w)
+
+
+def test_lattice_degeneracies(api):
+    """Tiny lattice polygons with repeated vertices, collinear runs, horizontal edges,
+    self-intersections and an explicit closing vertex; every lattice point of [-1, 17]^2."""
+    rng = np.random.default_rng(5)
+    polys = []
+    for t in range(300):
+        m = int(rng.integers(3, 9))
+        v = [tuple(map(int, rng.integers(0, 17, 2))) for _ in range(m)]
+        if t % 4 == 1:
+            v = v[:2] + [v[1]] + v[2:]
+        elif t % 4 == 2:
+            v = v + [(int(rng.integers(0, 17)), v[-1][1])]
+        elif t % 4 == 3:
+            v = v + [v[0]]
+        polys.append(v)
+    xs, ys = np.meshgrid(np.arange(-1, 18), np.arange(-1, 18))
+    pts = np.stack([xs.ravel(), ys.ravel()], 1)
+    check_full(api, make("lattice", polys, pts))
+
+
+def test_degenerate_polygons_and_empty_lists(api):
+    rng = np.random.default_rng(6)
+    polys = [[], [(1, 1)], [(0, 0), (5, 5)], [(0, 0), (4, 0), (0, 4)], [], [(0, 0), (9, 0), (9, 9), (0, 9)]]
+    pts = rng.integers(-1, 11, size=(200, 2))
+    csr = [list(range(0, 50)), [], list(range(10, 90)), list(range(200)), list(range(5)), list(range(199, -1, -1))]
+    check_full(api, make("degenerate-csr", polys, pts, csr))
+    check_full(api, make("degenerate-dense", polys, pts))
+
+
+def test_int32_extremes(api):
+    lo, hi = -2**31, 2**31 - 1
+    polys = [[(lo, lo), (hi, lo), (hi, hi), (lo, hi)],
+             [(lo, lo), (hi, hi), (lo, hi)],
+             [(lo, 0), (0, lo), (hi, 0), (0, hi)],
+             [(lo, lo), (hi, lo + 1), (lo + 2, hi)]]
+    pts = [(lo, lo), (hi, hi), (lo, hi), (hi, lo), (0, 0), (lo + 1, lo), (hi - 1, hi - 1), (lo, 0), (hi, 0),
+           (-1, -1), (1, 1), (lo + 1, lo + 1), (0, lo), (0, hi), (hi - 1, lo)]
+    rng = np.random.default_rng(7)
+    pts += [tuple(map(int, rng.integers(lo, hi, 2, endpoint=True))) for _ in range(400)]
+    check_full(api, make("extremes", polys, pts))
+
+
+def test_many_empty_polygons_in_one_chunk(api):
+    """A chunk of candidates whose owning polygons are spread over more than one window of
+    polygon offsets (hundreds of polygons with no candidates in between)."""
+    rng = np.random.default_rng(8)
+    polys, csr = [], []
+    for k in range(3000):
+        cx, cy = int(rng.integers(0, 10**6)), int(rng.integers(0, 10**6))
+        m = int(rng.integers(3, 9))
+        ang = np.sort(rng.uniform(0, 2 * np.pi, m))
+        polys.append([(cx + int(300 * np.cos(a)), cy + int(300 * np.sin(a))) for a in ang])
+        csr.append([] if k % 7 else list(rng.integers(0, 5000, int(rng.integers(0, 3)))))
+    pts = rng.integers(0, 10**6, size=(5000, 2))
+    for k in range(0, 3000, 7):   # give listed candidates a chance to be inside
+        for j, pid in enumerate(csr[k]):
+            pts[pid] = polys[k][0][0] - 10, polys[k][0][1]
+    check_full(api, make("sparse-csr", polys, pts, csr))
+
+
+@pytest.mark.parametrize("tuning", [(256, 1, 1), (512, 2, 2), (1024, 4, 2), (2048, 2, 3), (6144, 1, 1)])
+def test_tuning_shapes(api, tuning):
+    """Every tuned shape gives the same bits (small edge tiles force the streamed path)."""
+    before = api.pip_get_tuning()
+    api.pip_set_tuning(*tuning)
+    try:
+        w = W.footprints(seed=11, n_polys=4000, pts_per_poly=16)
+        check_full(api, w, f"tuning={tuning}")
+        big = W.fractal(seed=12, n_polys=4, m_lo=3000, m_hi=9000, n_points=30000, cell=200_000, grid=2)
+        check_full(api, big, f"tuning={tuning}")
+        s = W.star(seed=13, m=1024, n_uniform=4000, n_special=300)
+        check_full(api, s, f"tuning={tuning}")
+    finally:
+        api.pip_set_tuning(*before)
+
+
+# ------------------------------------------------------------------------------------------
+# the five workloads
+# ------------------------------------------------------------------------------------------
+
+def test_star_full(api):
+    w = W.star()
+    check_full(api, w)
+
+
+def test_footprints_reduced(api):
+    check_full(api, W.footprints(n_polys=50_000))
+
+
+def test_footprints_scattered_points(api):
+    check_full(api, W.scattered_points(W.footprints(seed=21, n_polys=20_000)))
+
+
+def test_stress_reduced(api):
+    check_full(api, W.stress(n_polys=60_000))
+
+
+def test_fractal_reduced(api):
+    w = W.fractal(n_polys=6, m_lo=5_000, m_hi=40_000, n_points=150_000, cell=400_000, grid=3)
+    check_full(api, w)
+
+
+def test_join_reduced(api):
+    """Binning then classification: the GPU candidate sets equal the oracle's closed-bbox sets
+    polygon by polygon, and classification of that CSR matches the oracle."""
+    w = W.join(n_polys=3000, n_points=300_000)
+    d = api.to_device(w)
+    co, ids = api.bin_join(d["points"], d["poly_offsets"], d["verts"])
+    torch.cuda.synchronize()
+    co = co.cpu().numpy()
+    ids = ids.cpu().numpy()
+    counts, want_ids = oracle.bbox_join(w.points, w.poly_offsets, w.verts, np.arange(w.n_polys))
+    assert np.array_equal(np.diff(co.astype(np.int64)), counts)
+    pos = 0
+    for k in range(w.n_polys):
+        a = np.sort(ids[co[k]:co[k + 1]])
+        assert np.array_equal(a, want_ids[pos:pos + counts[k]]), f"polygon {k}"
+        pos += counts[k]
+    # classification parity on the oracle's own candidate lists (no oracle input from the GPU)
+    oco = np.zeros(w.n_polys + 1, dtype=np.int64)
+    oco[1:] = np.cumsum(counts)
+    check_full(api, w.with_csr(oco, want_ids), "joined")
+
+
+def test_binning_is_deterministic(api):
+    w = W.join(seed=31, n_polys=2000, n_points=200_000)
+    d = api.to_device(w)
+    co1, ids1 = api.bin_join(d["points"], d["poly_offsets"], d["verts"])
+    co2, ids2 = api.bin_join(d["points"], d["poly_offsets"], d["verts"])
+    torch.cuda.synchronize()
+    assert torch.equal(co1, co2) and torch.equal(ids1, ids2)
