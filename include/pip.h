@@ -75,10 +75,13 @@ typedef struct pip_stats {
 } pip_stats;
 
 /*
- * pip_classify -- the FP32-filtered persistent kernel (Method, steps 2-7; Constraint 1).
+ * pip_classify -- the FP32-filtered batched kernels (Method, steps 2-7; Constraint 1).
  * Each polygon is rebased to a local frame; the side test (p - R_i) . n runs in FP32 with
  * a proven forward-error bound, and any (point, edge) pair whose FP32 value lies within
  * the bound is re-tested exactly with 64/128-bit integers, so the result is exact.
+ * Polygons of up to 120 vertices run in a warp-per-candidate-segment kernel, larger ones in
+ * a second kernel that splits their edges across CTAs (two launches on `stream`).  The
+ * first call on a stream allocates that stream's work list and must not be captured.
  * Arguments and output layout as described above.  Returns PIP_OK or PIP_ERR_*.
  */
 int pip_classify(const int32_t *points, int64_t n_points,
@@ -128,14 +131,16 @@ int pip_bin_fill(const int32_t *points, int64_t n_points,
                  int32_t *d_overflow, void *stream);
 
 /*
- * Tuning of pip_classify (the autotuner's hook; not in the paper).  edge_tile: edges staged
- * in shared memory per pass (256..8192, multiple of 32); pts_per_thread: candidates each
- * thread carries through the edge loop (1, 2 or 4); ctas_per_sm: resident CTAs per SM for
- * the persistent grid (1..8).  0 keeps the current value.  Applies to later calls on every
- * device; returns PIP_ERR_INVALID for an out-of-range value.
+ * Tuning of pip_classify (the autotuner's hook; not in the paper).  0 keeps a value.
+ *   edge_tile      large-polygon kernel: edges staged in shared memory per pass
+ *                  (256..8192, a multiple of 32)
+ *   pts_per_warp   small-polygon kernel: candidates a warp takes per group (64, 128, 256)
+ *   ctas_per_sm    large-polygon kernel: resident CTAs per SM (1..8)
+ *   pts_per_thread large-polygon kernel: candidates each thread carries (1, 2, 4)
+ * Applies to later calls on every device; PIP_ERR_INVALID for an out-of-range value.
  */
-int pip_set_tuning(int32_t edge_tile, int32_t pts_per_thread, int32_t ctas_per_sm);
-int pip_get_tuning(int32_t *edge_tile, int32_t *pts_per_thread, int32_t *ctas_per_sm);
+int pip_set_tuning(int32_t edge_tile, int32_t pts_per_warp, int32_t ctas_per_sm, int32_t pts_per_thread);
+int pip_get_tuning(int32_t *edge_tile, int32_t *pts_per_warp, int32_t *ctas_per_sm, int32_t *pts_per_thread);
 
 /* Statistics (device counters of the current device).  pip_get_stats copies them to the
  * host with a synchronous copy: call it after the work of interest has completed. */

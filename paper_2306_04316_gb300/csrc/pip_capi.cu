@@ -3,6 +3,7 @@
 #include <atomic>
 #include <climits>
 #include <cstring>
+#include <map>
 #include <mutex>
 
 #include "pip.h"
@@ -14,17 +15,20 @@ using namespace pipdev;
 namespace {
 
 constexpr int MAX_DEVICES = 64;
+constexpr int LARGE_LIST_CAP = 1 << 16;   // polygons per call handed to the large-polygon kernel
 
 struct DeviceState {
     unsigned long long *stats = nullptr;   // ST_COUNT counters
     int n_sm = 0;
+    std::map<cudaStream_t, LargeList *> lists;   // one large-polygon list per stream
 };
 
 std::mutex g_mu;
 DeviceState g_dev[MAX_DEVICES];
 std::atomic<int> g_edge_tile{2048};
+std::atomic<int> g_ppw{128};
+std::atomic<int> g_ctas{2};
 std::atomic<int> g_ppt{2};
-std::atomic<int> g_ctas{3};
 thread_local int g_last_cuda = 0;
 
 int cuda_fail(cudaError_t e)
@@ -63,6 +67,28 @@ int device_state(cudaStream_t stream, DeviceState **out)
         s.stats = p;
     }
     *out = &s;
+    return PIP_OK;
+}
+
+// The large-polygon list of (current device, stream): created zeroed on the first call on
+// that stream, which must not be made during stream capture.
+int stream_list(DeviceState *ds, cudaStream_t stream, LargeList **out)
+{
+    std::lock_guard<std::mutex> lock(g_mu);
+    auto it = ds->lists.find(stream);
+    if (it != ds->lists.end()) {
+        *out = it->second;
+        return PIP_OK;
+    }
+    if (capturing(stream)) return PIP_ERR_WORKSPACE;
+    const size_t bytes = sizeof(LargeList) + (size_t)LARGE_LIST_CAP * 2 * sizeof(int);
+    void *p = nullptr;
+    cudaError_t e = cudaMalloc(&p, bytes);
+    if (e != cudaSuccess) return cuda_fail(e);
+    e = cudaMemset(p, 0, bytes);
+    if (e != cudaSuccess) { cudaFree(p); return cuda_fail(e); }
+    ds->lists[stream] = static_cast<LargeList *>(p);
+    *out = static_cast<LargeList *>(p);
     return PIP_OK;
 }
 
@@ -120,10 +146,13 @@ int pip_classify(const int32_t *points, int64_t n_points, const int32_t *poly_of
     DeviceState *ds = nullptr;
     rc = device_state(s, &ds);
     if (rc != PIP_OK) return rc;
+    LargeList *ll = nullptr;
+    rc = stream_list(ds, s, &ll);
+    if (rc != PIP_OK) return rc;
     ClassifyArgs a = make_args(points, n_points, poly_offsets, verts, n_polys, cand_offsets, cand_ids,
                                out_bits, ds->stats);
-    Tuning t{g_edge_tile.load(), g_ppt.load(), g_ctas.load()};
-    int e = launch_filtered(a, total_bits, t, ds->n_sm, s);
+    Tuning t{g_edge_tile.load(), g_ppw.load(), g_ctas.load(), g_ppt.load()};
+    int e = launch_filtered(a, total_bits, t, ds->n_sm, ll, LARGE_LIST_CAP, s);
     return e == 0 ? PIP_OK : cuda_fail((cudaError_t)e);
 }
 
@@ -150,24 +179,28 @@ int pip_classify_exact(const int32_t *points, int64_t n_points, const int32_t *p
     return e == 0 ? PIP_OK : cuda_fail((cudaError_t)e);
 }
 
-int pip_set_tuning(int32_t edge_tile, int32_t pts_per_thread, int32_t ctas_per_sm)
+int pip_set_tuning(int32_t edge_tile, int32_t pts_per_warp, int32_t ctas_per_sm, int32_t pts_per_thread)
 {
-    if (edge_tile != 0 && (edge_tile < 256 || edge_tile > 6144 || edge_tile % 32 != 0)) return PIP_ERR_INVALID;
-    if (pts_per_thread != 0 && pts_per_thread != 1 && pts_per_thread != 2 && pts_per_thread != 4)
+    if (edge_tile != 0 && (edge_tile < 256 || edge_tile > 8192 || edge_tile % 32 != 0)) return PIP_ERR_INVALID;
+    if (pts_per_warp != 0 && pts_per_warp != 64 && pts_per_warp != 128 && pts_per_warp != 256)
         return PIP_ERR_INVALID;
     if (ctas_per_sm != 0 && (ctas_per_sm < 1 || ctas_per_sm > 8)) return PIP_ERR_INVALID;
+    if (pts_per_thread != 0 && pts_per_thread != 1 && pts_per_thread != 2 && pts_per_thread != 4)
+        return PIP_ERR_INVALID;
     if (edge_tile) g_edge_tile.store(edge_tile);
-    if (pts_per_thread) g_ppt.store(pts_per_thread);
+    if (pts_per_warp) g_ppw.store(pts_per_warp);
     if (ctas_per_sm) g_ctas.store(ctas_per_sm);
+    if (pts_per_thread) g_ppt.store(pts_per_thread);
     return PIP_OK;
 }
 
-int pip_get_tuning(int32_t *edge_tile, int32_t *pts_per_thread, int32_t *ctas_per_sm)
+int pip_get_tuning(int32_t *edge_tile, int32_t *pts_per_warp, int32_t *ctas_per_sm, int32_t *pts_per_thread)
 {
-    if (!edge_tile || !pts_per_thread || !ctas_per_sm) return PIP_ERR_NULL;
+    if (!edge_tile || !pts_per_warp || !ctas_per_sm || !pts_per_thread) return PIP_ERR_NULL;
     *edge_tile = g_edge_tile.load();
-    *pts_per_thread = g_ppt.load();
+    *pts_per_warp = g_ppw.load();
     *ctas_per_sm = g_ctas.load();
+    *pts_per_thread = g_ppt.load();
     return PIP_OK;
 }
 

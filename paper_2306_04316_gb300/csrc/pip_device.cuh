@@ -27,6 +27,35 @@ enum StatIdx {
     ST_COUNT = 8
 };
 
+// Device-side list of polygons too large for a warp tile, filled by the batched kernel
+// and consumed by the large-polygon kernel.  Header followed by `cap` entries and `cap`
+// per-entry work counters.  The large-polygon kernel's last CTA resets the header, so the
+// list is empty between calls.
+struct LargeList {
+    int count;     // entries appended
+    int cursor;    // first entry whose work items are not all taken
+    int done;      // CTAs of the large-polygon kernel that have finished
+    int overflow;  // an append found the list full
+    int pad[4];
+};
+
+__device__ __forceinline__ int *large_entries(LargeList *l) { return reinterpret_cast<int *>(l + 1); }
+__device__ __forceinline__ int *large_taken(LargeList *l, int cap) { return reinterpret_cast<int *>(l + 1) + cap; }
+
+// 8- and 4-byte asynchronous global -> shared copies (LDGSTS) and their group fences.
+__device__ __forceinline__ void cp_async8(void *smem_dst, const void *gmem_src)
+{
+    const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(gmem_src) : "memory");
+}
+__device__ __forceinline__ void cp_async4(void *smem_dst, const void *gmem_src)
+{
+    const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(gmem_src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
 struct ClassifyArgs {
     const int2 *points;
     long long n_points;

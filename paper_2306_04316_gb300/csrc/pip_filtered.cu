@@ -1,4 +1,4 @@
-// FP32-filtered persistent kernel with an exact integer recheck.
+// FP32-filtered classification with an exact integer recheck (pip_classify).
 //
 // Method section, steps 2-7 with Constraint 1.  For the edge R_i -> R_j of a polygon and a
 // candidate point p, the crossing counts when the straddle test (y_i > p_y) != (y_j > p_y)
@@ -6,51 +6,61 @@
 // is the paper's side test (p - R_i) . n up to the sign fixed by orienting n so that
 // n_x >= 0.  Parity of the count = inside bit.
 //
-// Local frame and FP32 evaluation.  Every polygon (or, for polygons too large for one
-// shared-memory pass, every tile of edges together with the tile's candidate points) gets
-// an integer origin o at the centre of a box that holds all vertices and points used with
-// it; M_x, M_y bound |x - o_x|, |y - o_y| over that box.  Per edge the staging pass stores
-//     c' = s (X_i d_y - Y_i d_x)   (X = x - o_x, Y = y - o_y, s = sign(d_y); int64 exact,
-//                                   rounded once to FP32; double for frames >= 2^30)
-//     a = |d_y|,  b = s d_x        (rounded to FP32)
-//     B = 8.5 * 2^-24 (M_x |d_y| + M_y |d_x|)   (FP32, every operation rounded upward)
+// Local frame and FP32 evaluation.  A polygon (or one tile of a large polygon together with
+// the tile's candidate points) gets an integer origin o at the centre of a box holding every
+// vertex and point used with it; M_x, M_y bound |x - o_x|, |y - o_y| over that box.  Per
+// edge the staging pass stores
+//     c' = s (X_i d_y - Y_i d_x)   (X = x - o_x, Y = y - o_y, s = sign(d_y))
+//     a = |d_y|,  b = s d_x
 // and per (point, edge) pair the kernel evaluates t = fma(P_y, b, fma(-P_x, a, c')) with
-// P = p - o rounded to FP32, so that t approximates s * det.  Forward error: with
-// S = M_x |d_y| + M_y |d_x| and u = 2^-24, rounding c' costs <= (u + 2^-51) S, rounding
-// P_x, P_y, a, b costs <= (2u + u^2) S in the two products, and the two fused operations
-// cost <= u (2 + 4u) S and <= u (3 + 8u) S; in total < 8.01 u S <= B.  Hence |t| > B
-// implies sign(t) = sign(s det) and det != 0, and only pairs with a straddle and |t| <= B
-// need the exact 64/128-bit recheck, which the kernel runs in place.  Points outside
-// their polygon's closed bounding box are outside the polygon (the count of straddling
-// edges is even and all crossings lie on one side of p), so they skip the edge loop.
+// P = p - o rounded to FP32, so that t approximates s * det.
+//   * k_pip_large forms c' exactly (int64, or double when M >= 2^30) and rounds it once.
+//     With S = M_x |d_y| + M_y |d_x| and u = 2^-24, rounding c' costs <= (u + 2^-51) S,
+//     rounding P_x, P_y, a, b costs <= (2u + u^2) S in the two products, and the two fused
+//     operations cost <= u (2 + 4u) S and <= u (3 + 8u) S: in total < 8.01 u S, dominated by
+//     the per-edge bound B_e = 8.5 u S.
+//   * k_pip_poly forms the record in FP32 (see PM_BOUND_K): the error is below
+//     12u (M_x H + M_y W) with H, W the polygon's height and width, dominated by the
+//     polygon-wide bound B = 13 u (M_x H + M_y W).
+// Every bound is evaluated with upward rounding.  |t| > B implies sign(t) = sign(s det) and
+// det != 0; only a straddling pair with |t| <= B needs the exact 64/128-bit recheck, which
+// runs in place.  A point outside its polygon's closed bounding box is outside the polygon
+// (the number of straddling edges is even and every crossing lies on one side of p), so it
+// skips the edge loop.
 //
-// Work decomposition.  Candidates are cut into chunks of 256 * PPT consecutive candidates
-// (whole output words).  A persistent CTA takes chunks in a strided order; a warp finds the
-// polygon owning the chunk's first candidate with 32-way probes of cand_offsets; the CTA
-// stages the offsets of the next 256 polygons, then the vertices of as many whole polygons
-// as fit in a tile of T edges, computes each polygon's frame (bounding box by shared-memory
-// atomics) and edge records, and every thread walks its candidates' polygons' edges from
-// shared memory.  A polygon with more than T edges streams through shared memory in tiles,
-// each tile framed by the union of its vertices and the chunk's candidate points; parities
-// of the tiles combine by XOR.  Each warp packs its 32 parities with a ballot and writes
-// whole words (a chunk owns its words, so no atomics are needed).
+// Two kernels, launched back to back on the caller's stream:
+//
+// k_pip_poly -- polygon-major.  A CTA takes a chunk of 128 consecutive polygons, so that every
+//   array it reads is one contiguous range: the chunk's vertex and candidate offsets, its
+//   vertices and its candidate ids; only the candidate points are gathered (cp.async into
+//   shared memory).  It stages runs of whole polygons (up to 1,024 vertices per pass), computes
+//   each polygon's bounding box, frame and bound (thread per polygon) and the edge records
+//   (thread per edge), then classifies the run's candidates (thread per candidate, passes of
+//   2,048) against the records in shared memory.  Results are packed by warp ballots into
+//   shared words and written out; the first and last word of a pass may be shared with a
+//   neighbouring chunk, so those are written with a masked AND/OR pair that sets exactly the
+//   pass's own bits (no zero-fill pass is needed).  Polygons with more than 1,024 vertices or
+//   more than 2^18 (candidate, edge) pairs get bit 0 here and go on a device-side list.
+//
+// k_pip_large -- the listed polygons.  Work items (polygon, block of 256*PPT candidates,
+//   slice of edges) are taken from the list by atomic counters; the CTA streams the slice
+//   through shared memory in tiles of T edges, each tile framed by the union of its vertices
+//   and the block's candidate points, and XORs the partial parities into the output words
+//   (stream order puts it after the first kernel's writes).  Its last CTA empties the list for
+//   the next call.  With more large polygons than the list holds, it falls back to a scan over
+//   all polygons.
 #include <algorithm>
+#include <type_traits>
 
 #include "pip_device.cuh"
 #include "pip_launch.h"
 
 namespace pipdev {
 
-constexpr int FT_THREADS = 256;
-constexpr int FT_WIN = 256;                              // polygons per offsets window
 constexpr float FT_BOUND_K = 5.066394805908203125e-07f;  // 8.5 * 2^-24 (exact in FP32)
 
-size_t filtered_smem_bytes(int T)
-{
-    // records float4[T], vertices int2[T + 1], next-y int[T], vertex owner ushort[T]
-    size_t b = (size_t)T * 16 + (size_t)(T + 1) * 8 + (size_t)T * 4 + (size_t)T * 2;
-    return (b + 15) & ~(size_t)15;
-}
+// large-polygon kernel geometry
+constexpr int LG_THREADS = 256;
 
 struct Frame {
     int ox, oy;
@@ -61,10 +71,10 @@ struct Frame {
 __device__ __forceinline__ Frame make_frame(int xmin, int ymin, int xmax, int ymax)
 {
     Frame f;
-    long long ox = (long long)xmin + (((long long)xmax - xmin) >> 1);
-    long long oy = (long long)ymin + (((long long)ymax - ymin) >> 1);
-    long long Mx = max((long long)xmax - ox, ox - xmin);
-    long long My = max((long long)ymax - oy, oy - ymin);
+    const long long ox = (long long)xmin + (((long long)xmax - xmin) >> 1);
+    const long long oy = (long long)ymin + (((long long)ymax - ymin) >> 1);
+    const long long Mx = max((long long)xmax - ox, ox - xmin);
+    const long long My = max((long long)ymax - oy, oy - ymin);
     f.ox = (int)ox;
     f.oy = (int)oy;
     f.mx = __ll2float_ru(Mx);
@@ -73,13 +83,9 @@ __device__ __forceinline__ Frame make_frame(int xmin, int ymin, int xmax, int ym
     return f;
 }
 
-// Edge record of R_i -> R_j in frame f: (c', |d_y|, s d_x, B).  Horizontal edges never
-// straddle, so their record is never used for a decision.
-__device__ __forceinline__ float4 make_record(int2 ri, int2 rj, int ox, int oy, float mx, float my,
-                                              int wide)
+// c' = s (X_i d_y - Y_i d_x) rounded to FP32 (s = sign(d_y)).
+__device__ __forceinline__ float edge_c(int2 ri, long long dx, long long dy, int ox, int oy, int wide)
 {
-    const long long dx = (long long)rj.x - ri.x, dy = (long long)rj.y - ri.y;
-    if (dy == 0) return make_float4(0.f, 0.f, 0.f, 0.f);
     const long long X = (long long)ri.x - ox, Y = (long long)ri.y - oy;
     float c;
     if (!wide) {
@@ -87,27 +93,369 @@ __device__ __forceinline__ float4 make_record(int2 ri, int2 rj, int ox, int oy, 
     } else {
         c = __double2float_rn(__dmul_rn((double)X, (double)dy) - __dmul_rn((double)Y, (double)dx));
     }
-    const long long ady = dy > 0 ? dy : -dy;
-    const long long adx = dx >= 0 ? dx : -dx;
-    const float B = __fmul_ru(FT_BOUND_K, __fadd_ru(__fmul_ru(mx, __ll2float_ru(ady)),
-                                                    __fmul_ru(my, __ll2float_ru(adx))));
-    return make_float4(dy > 0 ? c : -c, __ll2float_rn(ady), __ll2float_rn(dy > 0 ? dx : -dx), B);
+    return dy > 0 ? c : -c;
 }
 
-// Parity over edges [e0, e1) of the staged tile.  Edge e runs from s_v[e] to s_v[nx(e)],
-// nx(e) = e + 1, or e0 for the last edge when `wrap` (a whole polygon in the tile).
-__device__ __forceinline__ int tile_parity(const float4 *__restrict__ s_rec, const int *__restrict__ s_yn,
-                                           const int2 *__restrict__ s_v, int e0, int e1, bool wrap,
-                                           int2 p, int ox, int oy, unsigned long long &n_fb_pts,
+__device__ __forceinline__ float bound_of(float mx, float my, long long adx, long long ady)
+{
+    return __fmul_ru(FT_BOUND_K, __fadd_ru(__fmul_ru(mx, __ll2float_ru(ady)), __fmul_ru(my, __ll2float_ru(adx))));
+}
+
+// Large-kernel edge record: (c', |d_y|, s d_x, B_e).  Horizontal edges never straddle.
+__device__ __forceinline__ float4 make_record(int2 ri, int2 rj, const Frame &f)
+{
+    const long long dx = (long long)rj.x - ri.x, dy = (long long)rj.y - ri.y;
+    if (dy == 0) return make_float4(0.f, 0.f, 0.f, 0.f);
+    const long long ady = dy > 0 ? dy : -dy, adx = dx >= 0 ? dx : -dx;
+    return make_float4(edge_c(ri, dx, dy, f.ox, f.oy, f.wide), __ll2float_rn(ady),
+                       __ll2float_rn(dy > 0 ? dx : -dx), bound_of(f.mx, f.my, adx, ady));
+}
+
+// Edge record of a frame 2^30 or more wide (int64 and double arithmetic; rare, out of line).
+__device__ __noinline__ float4 wide_record(int2 ri, int2 rj, int ox, int oy)
+{
+    const long long dx = (long long)rj.x - ri.x, dy = (long long)rj.y - ri.y;
+    const float c = dy == 0 ? 0.f : edge_c(ri, dx, dy, ox, oy, 1);
+    return dy > 0 ? make_float4(c, __ll2float_rn(dy), __ll2float_rn(dx), __int_as_float(rj.y))
+                  : make_float4(c, __ll2float_rn(-dy), __ll2float_rn(-dx), __int_as_float(rj.y));
+}
+
+
+// Exact parity of p over the edges e0..e1-1 of staged vertices v, edge e running from v[e]
+// to v[e + 1], or to v[e0] for the last edge when `wrap`.  Rare path: kept out of line.
+__device__ __noinline__ int exact_parity(const int2 *v, int e0, int e1, bool wrap, int2 p)
+{
+    int parity = 0;
+    for (int e = e0; e < e1; ++e) {
+        const int nx = (wrap && e + 1 == e1) ? e0 : e + 1;
+        const int2 ri = v[e], rj = v[nx];
+        if ((ri.y > p.y) != (rj.y > p.y)) parity ^= exact_edge_counts(p.x, p.y, ri.x, ri.y, rj.x, rj.y);
+    }
+    return parity;
+}
+
+// =============================================================================================
+// k_pip_poly
+// =============================================================================================
+
+// Bound factor of the FP32 records: rounding the four record inputs, the product Y d_x and the
+// fused X d_y - Y d_x, then P_x, P_y and the two per-pair fused operations, costs at most
+// 5u|X d_y| + 6u|Y d_x| + 4u|P_x d_y| + 3u|P_y d_x| (+ O(u^2)) <= 12u (M_x H + M_y W), with H, W
+// the polygon's height and width (>= |d_y|, |d_x| of every edge).
+constexpr float PM_BOUND_K = 7.748603820800781e-07f;     // 13 * 2^-24 (exact in FP32)
+constexpr int PM_THREADS = 256;
+constexpr int PM_NP = 128;          // polygons per chunk
+constexpr int PM_TV = 1024;         // staged vertices per pass
+constexpr int PM_TC = 2048;         // staged candidates per pass
+constexpr int PM_LARGE_M = 1024;    // polygons above this many vertices go to k_pip_large
+constexpr long long PM_LARGE_W = 1LL << 18;   // ... and those with more (candidates x vertices)
+
+struct __align__(16) PolySmem {
+    float4 rec[PM_TV];              // edge records
+    int2 v[PM_TV + 1];              // raw vertices
+    int2 pts[PM_TC];                // candidate points
+    int4 pbox[PM_NP];               // bounding box per chunk polygon
+    int4 pfr[PM_NP];                // frame: ox, oy, bound (float bits), wide
+    unsigned short vp[PM_TV];       // vertex -> chunk polygon
+    unsigned short cp[PM_TC];       // candidate -> chunk polygon (0xffff: padding)
+    unsigned short queue[PM_TC];    // candidates inside their polygon's box
+    int ids[PM_TC];                 // candidate ids of the pass (CSR)
+    int co32[PM_NP + 1];            // candidate offsets as loaded (CSR)
+    unsigned words[PM_TC / 32 + 2]; // result bits of the candidate pass
+    long long co[PM_NP + 1];        // candidate offsets of the chunk's polygons
+    int po[PM_NP + 1];              // vertex offsets
+    unsigned lg[PM_NP / 32];        // bit q: chunk polygon q goes to k_pip_large
+    int run_end, nq;
+};
+
+__device__ __forceinline__ bool pm_is_large(long long m, long long n)
+{
+    return m > PM_LARGE_M || m * n > PM_LARGE_W;
+}
+
+// Sets exactly the bits `mask` of *word to `bits` (other bits untouched, no zero-fill needed).
+__device__ __forceinline__ void masked_store(uint32_t *word, unsigned mask, unsigned bits)
+{
+    if (mask == 0xffffffffu) {
+        *word = bits;
+    } else if (mask) {
+        atomicAnd(word, ~mask | bits);
+        atomicOr(word, bits & mask);
+    }
+}
+
+template <bool DENSE>
+__global__ void __launch_bounds__(PM_THREADS, 4) k_pip_poly(ClassifyArgs a, long long total_bits, LargeList *ll,
+                                                            int lcap)
+{
+    using CI = typename std::conditional<DENSE, long long, int>::type;
+    extern __shared__ __align__(16) unsigned char dsm[];
+    PolySmem &sm = *reinterpret_cast<PolySmem *>(dsm);
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const int P = a.n_polys;
+    const CI W32 = (CI)(a.words_per_poly * 32);
+    const CI NPTS = (CI)a.n_points;
+    const int nchunk = (P + PM_NP - 1) / PM_NP;
+    unsigned st_cand = 0, st_rej = 0, st_fbp = 0;
+    if (!DENSE && blockIdx.x == 0 && tid == 0 && P > 0) {
+        // bits past the last candidate in the final word are 0
+        const long long C = __ldg(a.cand_offsets + P);
+        if (C & 31) masked_store(a.out_bits + (C >> 5), ~((1u << (C & 31)) - 1u), 0u);
+    }
+
+    for (int ch = blockIdx.x; ch < nchunk; ch += gridDim.x) {
+        const int k0 = ch * PM_NP;
+        const int np = min(PM_NP, P - k0);
+        if (tid < PM_NP / 32) sm.lg[tid] = 0;
+        for (int t = tid; t <= np; t += PM_THREADS) {
+            cp_async4(&sm.po[t], a.poly_offsets + k0 + t);
+            if (!DENSE) cp_async4(&sm.co32[t], a.cand_offsets + k0 + t);
+        }
+        cp_async_commit();
+        cp_async_wait_all();
+        __syncthreads();
+        for (int t = tid; t <= np; t += PM_THREADS)
+            sm.co[t] = DENSE ? (long long)(k0 + t) * W32 : (long long)sm.co32[t];
+        __syncthreads();
+        for (int q = tid; q < np; q += PM_THREADS) {
+            const long long n = DENSE ? min((long long)NPTS, (long long)W32) : sm.co[q + 1] - sm.co[q];
+            if (pm_is_large(sm.po[q + 1] - sm.po[q], n)) atomicOr(&sm.lg[q >> 5], 1u << (q & 31));
+        }
+        int pa = 0;
+        while (pa < np) {
+            __syncthreads();
+            // ---- warp 0: the next run of small polygons whose vertices fit one pass (or one
+            //      large polygon); lane l tests run end pa + 1 + l, ...
+            if (wid == 0) {
+                const bool large0 = (sm.lg[pa >> 5] >> (pa & 31)) & 1u;
+                int pb = pa + 1;
+                if (!large0) {
+                    for (int base = pa + 1; base <= np; base += 32) {
+                        const int q = base + lane;   // candidate end: polygons [pa, q)
+                        const bool ok = q <= np && sm.po[q] - sm.po[pa] <= PM_TV &&
+                                        !((sm.lg[(q - 1) >> 5] >> ((q - 1) & 31)) & 1u);
+                        const unsigned bm = __ballot_sync(FULL, ok);
+                        // ok is a prefix property (monotone) up to the first failure
+                        const unsigned run = ~bm ? (__ffs(~bm) - 1) : 32;
+                        pb = base + (int)run - 1;
+                        if (run < 32) break;
+                    }
+                    pb = max(pb, pa + 1);
+                }
+                if (lane == 0) sm.run_end = large0 ? -(pa + 1) : pb;
+            }
+            __syncthreads();
+            const bool large = sm.run_end < 0;
+            const int pb = large ? pa + 1 : sm.run_end;
+            const CI cbeg = (CI)sm.co[pa], cfin = (CI)sm.co[pb];
+            const int vbase = sm.po[pa];
+            if (large) {
+                // bits 0 here (k_pip_large XORs the parities in later); the list gets the polygon
+                if (tid == 0 && cfin > cbeg && NPTS > 0) {
+                    const int idx = atomicAdd(&ll->count, 1);
+                    if (idx < lcap) {
+                        large_entries(ll)[idx] = k0 + pa;
+                        large_taken(ll, lcap)[idx] = 0;
+                    } else {
+                        atomicExch(&ll->overflow, 1);
+                    }
+                }
+                const CI w0 = cbeg >> 5, w1 = (cfin + 31) >> 5;
+                for (CI wd = w0 + tid; wd < w1; wd += PM_THREADS) {
+                    const int lo = (int)(max(cbeg, wd * 32) - wd * 32), hi = (int)(min(cfin, wd * 32 + 32) - wd * 32);
+                    const unsigned mask = (hi >= 32 ? 0xffffffffu : ((1u << hi) - 1u)) & ~((1u << lo) - 1u);
+                    masked_store(a.out_bits + wd, mask, 0u);
+                }
+                pa = pb;
+                continue;
+            }
+            // ---- stage the run's vertices; bounding boxes and frames, one thread per polygon
+            const int nv = sm.po[pb] - vbase;
+            for (int i = tid; i < nv; i += PM_THREADS) cp_async8(&sm.v[i], a.verts + vbase + i);
+            cp_async_commit();
+            const int nc0 = (int)min((CI)PM_TC, cfin - cbeg);
+            if (!DENSE)   // the first pass's candidate ids travel with the vertices
+                for (int i = tid; i < nc0; i += PM_THREADS) cp_async4(&sm.ids[i], a.cand_ids + cbeg + i);
+            cp_async_commit();
+            cp_async_wait_all();
+            __syncthreads();
+            for (int q = pa + tid; q < pb; q += PM_THREADS) {
+                const int e0 = sm.po[q] - vbase, e1 = sm.po[q + 1] - vbase;
+                int x0 = INT_MAX, y0 = INT_MAX, x1 = INT_MIN, y1 = INT_MIN;
+                for (int i = e0; i < e1; ++i) {
+                    const int2 v = sm.v[i];
+                    x0 = min(x0, v.x); y0 = min(y0, v.y); x1 = max(x1, v.x); y1 = max(y1, v.y);
+                    sm.vp[i] = (unsigned short)q;
+                }
+                const unsigned W = (unsigned)x1 - (unsigned)x0, H = (unsigned)y1 - (unsigned)y0;
+                const unsigned Mx = W - (W >> 1), My = H - (H >> 1);
+                const float B = __fmul_ru(PM_BOUND_K, __fadd_ru(__fmul_ru(__uint2float_ru(Mx), __uint2float_ru(H)),
+                                                                 __fmul_ru(__uint2float_ru(My), __uint2float_ru(W))));
+                sm.pfr[q] = make_int4(x0 + (int)(W >> 1), y0 + (int)(H >> 1), __float_as_int(B),
+                                      (Mx >= (1u << 30)) | (My >= (1u << 30)));
+                sm.pbox[q] = make_int4(x0, y0, x1, y1);
+            }
+            __syncthreads();
+            // ---- edge records, one thread per edge (FP32 unless the frame is 2^30 wide)
+            for (int i = tid; i < nv; i += PM_THREADS) {
+                const int q = sm.vp[i];
+                const int nx = (i + 1 == sm.po[q + 1] - vbase) ? sm.po[q] - vbase : i + 1;
+                const int2 ri = sm.v[i], rj = sm.v[nx];
+                const int4 f = sm.pfr[q];
+                float4 rec;
+                if (!f.w) {
+                    const int dx = rj.x - ri.x, dy = rj.y - ri.y;
+                    const float fdx = __int2float_rn(dx), fdy = __int2float_rn(dy);
+                    const float X = __int2float_rn(ri.x - f.x), Y = __int2float_rn(ri.y - f.y);
+                    const float c = __fmaf_rn(X, fdy, -__fmul_rn(Y, fdx));
+                    rec = dy > 0 ? make_float4(c, fdy, fdx, __int_as_float(rj.y))
+                                 : make_float4(-c, -fdy, -fdx, __int_as_float(rj.y));
+                } else {
+                    rec = wide_record(ri, rj, f.x, f.y);
+                }
+                sm.rec[i] = rec;
+            }
+            // ---- the run's candidates, in passes of PM_TC
+            for (CI cb0 = cbeg; cb0 < cfin; cb0 += PM_TC) {
+                const int nc = (int)min((CI)PM_TC, cfin - cb0);
+                // points: cp.async gathers into shared memory (ids of later passes staged first)
+                if (!DENSE && cb0 != cbeg) {
+                    __syncthreads();
+                    for (int i = tid; i < nc; i += PM_THREADS) cp_async4(&sm.ids[i], a.cand_ids + cb0 + i);
+                    cp_async_commit();
+                    cp_async_wait_all();
+                    __syncthreads();
+                }
+                for (int i = tid; i < nc; i += PM_THREADS) {
+                    const CI c = cb0 + i;
+                    CI pid;
+                    if (DENSE) pid = c - (c / W32) * W32;
+                    else pid = sm.ids[i];
+                    if (pid < NPTS) cp_async8(&sm.pts[i], a.points + pid);
+                }
+                cp_async_commit();
+                // candidate -> polygon, one thread per polygon
+                for (int q = pa + tid; q < pb; q += PM_THREADS) {
+                    const int s0 = (int)(max((CI)sm.co[q], cb0) - cb0);
+                    const int s1 = (int)(min((CI)sm.co[q + 1], cb0 + nc) - cb0);
+                    int s1v = s1;
+                    if (DENSE) s1v = (int)max((CI)s0, min((CI)s1 + cb0, (CI)sm.co[q] + NPTS) - cb0);
+                    for (int s = s0; s < s1v; ++s) sm.cp[s] = (unsigned short)q;
+                    for (int s = s1v; s < s1; ++s) sm.cp[s] = 0xffff;   // dense padding
+                }
+                for (int t = tid; t < PM_TC / 32 + 2; t += PM_THREADS) sm.words[t] = 0;
+                if (tid == 0) sm.nq = 0;
+                cp_async_wait_all();
+                __syncthreads();
+                // queue the candidates inside their polygon's box
+                for (int i0 = 0; i0 < nc; i0 += PM_THREADS) {
+                    const int i = i0 + tid;
+                    bool q = false;
+                    if (i < nc) {
+                        const int pq = sm.cp[i];
+                        if (pq != 0xffff) {
+                            const int2 p = sm.pts[i];
+                            const int4 b = sm.pbox[pq];
+                            q = p.x >= b.x && p.x <= b.z && p.y >= b.y && p.y <= b.w;
+                            ++st_cand;
+                        }
+                    }
+                    const unsigned qm = __ballot_sync(FULL, q);
+                    int base = 0;
+                    if (lane == 0 && qm) base = atomicAdd(&sm.nq, __popc(qm));
+                    base = __shfl_sync(FULL, base, 0);
+                    if (q) sm.queue[base + __popc(qm & ((1u << lane) - 1u))] = (unsigned short)i;
+                }
+                __syncthreads();
+                const int nq = sm.nq;
+                st_rej -= (unsigned)(tid == 0 ? nq : 0);
+                // the edge loop, one queued candidate per thread
+                const int sh = (int)(cb0 & 31);   // bit of candidate cb0 within its word
+                for (int qi = tid; qi < nq; qi += PM_THREADS) {
+                    const int i = sm.queue[qi];
+                    const int pq = sm.cp[i];
+                    const int2 p = sm.pts[i];
+                    const int4 f = sm.pfr[pq];
+                    const int e0 = sm.po[pq] - vbase, e1 = sm.po[pq + 1] - vbase;
+                    const float B = __int_as_float(f.z);
+                    const float Px = __int2float_rn(p.x - f.x), Py = __int2float_rn(p.y - f.y);
+                    bool sp = sm.v[e0].y > p.y;
+                    int parity = 0;
+                    bool unc = false;
+                    #pragma unroll 2
+                    for (int e = e0; e < e1; ++e) {
+                        const float4 q4 = sm.rec[e];
+                        const bool sn = __float_as_int(q4.w) > p.y;
+                        const bool st = sn != sp;
+                        sp = sn;
+                        float t = __fmaf_rn(-Px, q4.y, q4.x);
+                        t = __fmaf_rn(Py, q4.z, t);
+                        parity ^= (int)(st & (t > 0.f));
+                        unc |= st & (fabsf(t) <= B);
+                    }
+                    if (unc) {
+                        ++st_fbp;
+                        parity = exact_parity(sm.v, e0, e1, true, p);
+                    }
+                    if (parity) {
+                        const int b = sh + i;
+                        atomicOr(&sm.words[b >> 5], 1u << (b & 31));
+                    }
+                }
+                __syncthreads();
+                // write the pass's words: bits [sh, sh + nc) of words cb0 >> 5 ...
+                const int nwd = (sh + nc + 31) >> 5;
+                for (int t = tid; t < nwd; t += PM_THREADS) {
+                    const int lo = t == 0 ? sh : 0;
+                    const int hi = min(32, sh + nc - 32 * t);
+                    const unsigned mask = (hi >= 32 ? 0xffffffffu : ((1u << hi) - 1u)) & ~((1u << lo) - 1u);
+                    masked_store(a.out_bits + (cb0 >> 5) + t, mask, sm.words[t]);
+                }
+                __syncthreads();
+            }
+            pa = pb;
+        }
+        __syncthreads();
+    }
+    if (a.stats) {
+        st_rej += st_cand;
+        #pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            st_cand += __shfl_down_sync(FULL, st_cand, o);
+            st_rej += __shfl_down_sync(FULL, st_rej, o);
+            st_fbp += __shfl_down_sync(FULL, st_fbp, o);
+        }
+        if (lane == 0) {
+            if (st_cand) atomicAdd(a.stats + ST_CANDIDATES, (unsigned long long)st_cand);
+            if (st_rej) atomicAdd(a.stats + ST_BBOX_REJECTS, (unsigned long long)st_rej);
+            if (st_fbp) atomicAdd(a.stats + ST_FALLBACK_POINTS, (unsigned long long)st_fbp);
+        }
+    }
+}
+
+// =============================================================================================
+// k_pip_large
+// =============================================================================================
+
+size_t filtered_smem_bytes(int T)
+{
+    // records float4[T], vertices int2[T + 1]
+    size_t b = (size_t)T * 16 + (size_t)(T + 1) * 8;
+    return (b + 15) & ~(size_t)15;
+}
+
+// Parity over the tile's edges 0..nt-1 (edge e from s_v[e] to s_v[e + 1]).
+__device__ __forceinline__ int tile_parity(const float4 *__restrict__ s_rec, const int2 *__restrict__ s_v, int nt,
+                                           int2 p, const Frame &f, unsigned long long &n_fb_pts,
                                            unsigned long long &n_fb_edges)
 {
-    const float Px = __ll2float_rn((long long)p.x - ox);
-    const float Py = __ll2float_rn((long long)p.y - oy);
-    bool sp = s_v[e0].y > p.y;
+    const float Px = __ll2float_rn((long long)p.x - f.ox);
+    const float Py = __ll2float_rn((long long)p.y - f.oy);
+    bool sp = s_v[0].y > p.y;
     int parity = 0, unc = 0;
-    for (int e = e0; e < e1; ++e) {
+    for (int e = 0; e < nt; ++e) {
         const float4 q = s_rec[e];
-        const bool s = s_yn[e] > p.y;
+        const bool s = s_v[e + 1].y > p.y;
         const bool st = s != sp;
         sp = s;
         float t = __fmaf_rn(-Px, q.y, q.x);
@@ -116,207 +464,151 @@ __device__ __forceinline__ int tile_parity(const float4 *__restrict__ s_rec, con
         unc += (int)(st & (fabsf(t) <= q.w));
     }
     if (unc) {
-        // some sign was within the error bound: redo this candidate exactly
         ++n_fb_pts;
         n_fb_edges += (unsigned long long)unc;
-        parity = 0;
-        for (int e = e0; e < e1; ++e) {
-            const int nx = (wrap && e + 1 == e1) ? e0 : e + 1;
-            const int2 ri = s_v[e], rj = s_v[nx];
-            if ((ri.y > p.y) != (rj.y > p.y)) parity ^= exact_edge_counts(p.x, p.y, ri.x, ri.y, rj.x, rj.y);
-        }
+        parity = exact_parity(s_v, 0, nt, false, p);
     }
     return parity;
 }
 
 template <int PPT>
-__global__ void __launch_bounds__(FT_THREADS) k_pip_filtered(ClassifyArgs a, long long total_bits, int T)
+__global__ void __launch_bounds__(LG_THREADS) k_pip_large(ClassifyArgs a, long long total_bits, LargeList *ll,
+                                                         int lcap, int T, int ES)
 {
     extern __shared__ __align__(16) unsigned char dsm[];
     float4 *s_rec = reinterpret_cast<float4 *>(dsm);
     int2 *s_v = reinterpret_cast<int2 *>(s_rec + T);
-    int *s_yn = reinterpret_cast<int *>(s_v + T + 1);
-    unsigned short *s_vp = reinterpret_cast<unsigned short *>(s_yn + T);
-
-    __shared__ long long s_co[FT_WIN + 1];
-    __shared__ int s_po[FT_WIN + 1];
-    __shared__ int s_bb[FT_WIN][4];
-    __shared__ Frame s_fr[FT_WIN];
+    __shared__ int s_item[4];          // polygon, candidate block, edge slice, valid
     __shared__ int s_pb[4], s_tb[4];
     __shared__ Frame s_tf;
-    __shared__ int s_k0;
 
-    constexpr int CH = FT_THREADS * PPT;
-    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    constexpr int CB = LG_THREADS * PPT;
+    const int tid = threadIdx.x, lane = tid & 31;
     const bool dense = a.cand_offsets == nullptr;
     const int P = a.n_polys;
-    const long long C = dense ? total_bits : (P > 0 ? (long long)__ldg(a.cand_offsets + P) : 0);
-    const long long nchunks = (C + CH - 1) / CH;
     const long long W32 = a.words_per_poly * 32;
-    const int end_v = P > 0 ? __ldg(a.poly_offsets + P) : 0;
-    unsigned long long st_cand = 0, st_rej = 0, st_fbp = 0, st_fbe = 0;
+    unsigned long long st_cand = 0, st_fbp = 0, st_fbe = 0;
+    const int count = *((volatile int *)&ll->count);
+    const bool scan = *((volatile int *)&ll->overflow) != 0;
+    long long scan_k = blockIdx.x;   // overflow mode: polygons blockIdx.x, + gridDim.x, ...
+    int scan_item = 0;
 
-    for (long long ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
-        const long long c0 = ch * CH, c1 = min(c0 + CH, C);
-        long long cc[PPT];
-        int2 pt[PPT];
-        int jj[PPT], par[PPT];
-        #pragma unroll
-        for (int r = 0; r < PPT; ++r) {
-            cc[r] = c0 + tid + r * FT_THREADS;
-            par[r] = 0;
-            pt[r] = make_int2(0, 0);
-            if (!dense && cc[r] < c1) pt[r] = __ldg(a.points + __ldg(a.cand_ids + cc[r]));
-        }
-        if (wid == 0) {
-            int k0 = dense ? (int)(c0 / W32) : warp_owner_search(a.cand_offsets, P, c0, lane);
-            if (lane == 0) s_k0 = k0 < 0 ? 0 : k0;
+    while (true) {
+        if (tid == 0) {
+            s_item[3] = 0;
+            if (!scan) {
+                while (true) {
+                    const int e = *((volatile int *)&ll->cursor);
+                    if (e >= min(count, lcap)) break;
+                    const int k = large_entries(ll)[e];
+                    const long long cs = dense ? k * W32 : (long long)a.cand_offsets[k];
+                    const long long ce = dense ? cs + W32 : (long long)a.cand_offsets[k + 1];
+                    const long long m = (long long)a.poly_offsets[k + 1] - a.poly_offsets[k];
+                    const long long nb = (ce - cs + CB - 1) / CB, ns = (m + ES - 1) / ES;
+                    const int it = atomicAdd(large_taken(ll, lcap) + e, 1);
+                    if ((long long)it < nb * ns) {
+                        s_item[0] = k; s_item[1] = (int)(it / ns); s_item[2] = (int)(it % ns); s_item[3] = 1;
+                        break;
+                    }
+                    atomicCAS(&ll->cursor, e, e + 1);
+                }
+            } else {
+                while (scan_k < P) {
+                    const int k = (int)scan_k;
+                    const long long cs = dense ? k * W32 : (long long)a.cand_offsets[k];
+                    const long long ce = dense ? cs + W32 : (long long)a.cand_offsets[k + 1];
+                    const long long m = (long long)a.poly_offsets[k + 1] - a.poly_offsets[k];
+                    const long long n = dense ? min((long long)a.n_points, W32) : ce - cs;
+                    const long long nb = pm_is_large(m, n) ? (ce - cs + CB - 1) / CB : 0, ns = (m + ES - 1) / ES;
+                    if (scan_item < nb * ns) {
+                        s_item[0] = k; s_item[1] = (int)(scan_item / ns); s_item[2] = (int)(scan_item % ns);
+                        s_item[3] = 1;
+                        ++scan_item;
+                        break;
+                    }
+                    scan_k += gridDim.x;
+                    scan_item = 0;
+                }
+            }
         }
         __syncthreads();
-        int kw = s_k0;
-        while (true) {
-            for (int j = tid; j <= FT_WIN; j += FT_THREADS) {
-                const long long k = (long long)kw + j;
-                if (k <= P) {
-                    s_co[j] = dense ? k * W32 : (long long)__ldg(a.cand_offsets + k);
-                    s_po[j] = __ldg(a.poly_offsets + k);
-                } else {
-                    s_co[j] = LLONG_MAX;
-                    s_po[j] = end_v;
-                }
-            }
-            __syncthreads();
-            const long long win_end = s_co[FT_WIN];
-            #pragma unroll
-            for (int r = 0; r < PPT; ++r) {
-                jj[r] = -1;
-                if (cc[r] < c1 && cc[r] >= s_co[0] && cc[r] < win_end) {
-                    const int j = upper_bound_dev(s_co, FT_WIN + 1, cc[r]) - 1;
-                    jj[r] = j;
-                    if (dense) {
-                        const long long pid = cc[r] - ((long long)kw + j) * W32;
-                        if (pid < a.n_points) pt[r] = __ldg(a.points + pid); else jj[r] = -1;
-                    }
-                    if (jj[r] >= 0) ++st_cand;
-                }
-            }
-            const int nw = min(FT_WIN, upper_bound_dev(s_co, FT_WIN + 1, c1 - 1));
-            int jb = 0;
-            while (jb < nw) {
-                const int base = s_po[jb];
-                // largest je in [jb, nw] with s_po[je] - base <= T
-                int lo = jb, hi = nw;
-                while (lo < hi) {
-                    const int mid = (lo + hi + 1) >> 1;
-                    if ((long long)s_po[mid] - base <= T) lo = mid; else hi = mid - 1;
-                }
-                const int je = lo;
-                if (je > jb) {
-                    // ---- small polygons [jb, je): whole polygons in one tile ----
-                    const int nv = s_po[je] - base;
-                    for (int i = tid; i < nv; i += FT_THREADS) {
-                        s_v[i] = __ldg(a.verts + base + i);
-                        s_vp[i] = (unsigned short)(jb + upper_bound_dev(s_po + jb, je - jb + 1, base + i) - 1);
-                    }
-                    for (int j = jb + tid; j < je; j += FT_THREADS) {
-                        s_bb[j][0] = INT_MAX; s_bb[j][1] = INT_MAX;
-                        s_bb[j][2] = INT_MIN; s_bb[j][3] = INT_MIN;
-                    }
-                    __syncthreads();
-                    for (int i = tid; i < nv; i += FT_THREADS) {
-                        const int j = s_vp[i];
-                        const int2 v = s_v[i];
-                        atomicMin(&s_bb[j][0], v.x); atomicMin(&s_bb[j][1], v.y);
-                        atomicMax(&s_bb[j][2], v.x); atomicMax(&s_bb[j][3], v.y);
-                    }
-                    __syncthreads();
-                    for (int j = jb + tid; j < je; j += FT_THREADS)
-                        if (s_po[j + 1] > s_po[j]) s_fr[j] = make_frame(s_bb[j][0], s_bb[j][1], s_bb[j][2], s_bb[j][3]);
-                    __syncthreads();
-                    for (int i = tid; i < nv; i += FT_THREADS) {
-                        const int j = s_vp[i];
-                        const int nx = (i + 1 == s_po[j + 1] - base) ? s_po[j] - base : i + 1;
-                        const Frame f = s_fr[j];
-                        const int2 rj = s_v[nx];
-                        s_rec[i] = make_record(s_v[i], rj, f.ox, f.oy, f.mx, f.my, f.wide);
-                        s_yn[i] = rj.y;
-                    }
-                    __syncthreads();
-                    #pragma unroll
-                    for (int r = 0; r < PPT; ++r) {
-                        const int j = jj[r];
-                        if (j >= jb && j < je) {
-                            const int e0 = s_po[j] - base, e1 = s_po[j + 1] - base;
-                            const int2 p = pt[r];
-                            if (e1 == e0 || p.x < s_bb[j][0] || p.x > s_bb[j][2] || p.y < s_bb[j][1] ||
-                                p.y > s_bb[j][3]) {
-                                ++st_rej;
-                                par[r] = 0;
-                            } else {
-                                const Frame f = s_fr[j];
-                                par[r] = tile_parity(s_rec, s_yn, s_v, e0, e1, true, p, f.ox, f.oy, st_fbp, st_fbe);
-                            }
-                        }
-                    }
-                    __syncthreads();
-                    jb = je;
-                } else {
-                    // ---- one polygon with more than T edges: stream its edges in tiles ----
-                    const int m = s_po[jb + 1] - base;
-                    if (tid == 0) { s_pb[0] = INT_MAX; s_pb[1] = INT_MAX; s_pb[2] = INT_MIN; s_pb[3] = INT_MIN; }
-                    __syncthreads();
-                    #pragma unroll
-                    for (int r = 0; r < PPT; ++r)
-                        if (jj[r] == jb) {
-                            atomicMin(&s_pb[0], pt[r].x); atomicMin(&s_pb[1], pt[r].y);
-                            atomicMax(&s_pb[2], pt[r].x); atomicMax(&s_pb[3], pt[r].y);
-                        }
-                    __syncthreads();
-                    const bool any = s_pb[0] <= s_pb[2];
-                    for (int e0 = 0; any && e0 < m; e0 += T) {
-                        const int nt = min(T, m - e0);
-                        if (tid == 0) {
-                            s_tb[0] = s_pb[0]; s_tb[1] = s_pb[1]; s_tb[2] = s_pb[2]; s_tb[3] = s_pb[3];
-                        }
-                        for (int i = tid; i <= nt; i += FT_THREADS) {
-                            int g = e0 + i;
-                            if (g >= m) g -= m;
-                            s_v[i] = __ldg(a.verts + base + g);
-                        }
-                        __syncthreads();
-                        for (int i = tid; i <= nt; i += FT_THREADS) {
-                            const int2 v = s_v[i];
-                            atomicMin(&s_tb[0], v.x); atomicMin(&s_tb[1], v.y);
-                            atomicMax(&s_tb[2], v.x); atomicMax(&s_tb[3], v.y);
-                        }
-                        __syncthreads();
-                        if (tid == 0) s_tf = make_frame(s_tb[0], s_tb[1], s_tb[2], s_tb[3]);
-                        __syncthreads();
-                        const Frame f = s_tf;
-                        for (int i = tid; i < nt; i += FT_THREADS) {
-                            const int2 rj = s_v[i + 1];
-                            s_rec[i] = make_record(s_v[i], rj, f.ox, f.oy, f.mx, f.my, f.wide);
-                            s_yn[i] = rj.y;
-                        }
-                        __syncthreads();
-                        #pragma unroll
-                        for (int r = 0; r < PPT; ++r)
-                            if (jj[r] == jb)
-                                par[r] ^= tile_parity(s_rec, s_yn, s_v, 0, nt, false, pt[r], f.ox, f.oy, st_fbp, st_fbe);
-                        __syncthreads();
-                    }
-                    jb += 1;
-                }
-            }
-            if (nw < FT_WIN || win_end >= c1) break;
-            kw += FT_WIN;
-            __syncthreads();
-        }
+        if (!s_item[3]) break;
+        const int k = s_item[0];
+        const long long cs = dense ? k * W32 : (long long)a.cand_offsets[k];
+        const long long ce = dense ? cs + W32 : (long long)a.cand_offsets[k + 1];
+        const long long cb0 = cs + (long long)s_item[1] * CB, cb1 = min(cb0 + CB, ce);
+        const int base = a.poly_offsets[k];
+        const int m = a.poly_offsets[k + 1] - base;
+        const int ea = s_item[2] * ES, eb = min(m, ea + ES);
+        int2 pt[PPT];
+        bool ok[PPT];
+        int par[PPT];
+        if (tid == 0) { s_pb[0] = INT_MAX; s_pb[1] = INT_MAX; s_pb[2] = INT_MIN; s_pb[3] = INT_MIN; }
+        __syncthreads();
         #pragma unroll
         for (int r = 0; r < PPT; ++r) {
-            const unsigned w = __ballot_sync(FULL, par[r]);
-            const long long word = (c0 + r * FT_THREADS + wid * 32) >> 5;
-            if (lane == 0 && (word << 5) < C) a.out_bits[word] = w;
+            const long long c = cb0 + tid + r * LG_THREADS;
+            ok[r] = c < cb1;
+            par[r] = 0;
+            pt[r] = make_int2(0, 0);
+            if (ok[r]) {
+                long long pid = dense ? c - (long long)k * W32 : (long long)__ldg(a.cand_ids + c);
+                if (pid >= a.n_points) ok[r] = false;
+                else pt[r] = __ldg(a.points + pid);
+            }
+            if (ok[r]) {
+                atomicMin(&s_pb[0], pt[r].x); atomicMin(&s_pb[1], pt[r].y);
+                atomicMax(&s_pb[2], pt[r].x); atomicMax(&s_pb[3], pt[r].y);
+                if (s_item[2] == 0) ++st_cand;
+            }
+        }
+        __syncthreads();
+        for (int e0 = ea; s_pb[0] <= s_pb[2] && e0 < eb; e0 += T) {
+            const int nt = min(T, eb - e0);
+            if (tid == 0) { s_tb[0] = s_pb[0]; s_tb[1] = s_pb[1]; s_tb[2] = s_pb[2]; s_tb[3] = s_pb[3]; }
+            for (int i = tid; i <= nt; i += LG_THREADS) {
+                int g = e0 + i;
+                if (g >= m) g -= m;
+                s_v[i] = __ldg(a.verts + base + g);
+            }
+            __syncthreads();
+            int x0 = INT_MAX, y0 = INT_MAX, x1 = INT_MIN, y1 = INT_MIN;
+            for (int i = tid; i <= nt; i += LG_THREADS) {
+                const int2 v = s_v[i];
+                x0 = min(x0, v.x); y0 = min(y0, v.y); x1 = max(x1, v.x); y1 = max(y1, v.y);
+            }
+            #pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                x0 = min(x0, __shfl_xor_sync(FULL, x0, o)); y0 = min(y0, __shfl_xor_sync(FULL, y0, o));
+                x1 = max(x1, __shfl_xor_sync(FULL, x1, o)); y1 = max(y1, __shfl_xor_sync(FULL, y1, o));
+            }
+            if (lane == 0) {
+                atomicMin(&s_tb[0], x0); atomicMin(&s_tb[1], y0); atomicMax(&s_tb[2], x1); atomicMax(&s_tb[3], y1);
+            }
+            __syncthreads();
+            if (tid == 0) s_tf = make_frame(s_tb[0], s_tb[1], s_tb[2], s_tb[3]);
+            __syncthreads();
+            const Frame f = s_tf;
+            for (int i = tid; i < nt; i += LG_THREADS) s_rec[i] = make_record(s_v[i], s_v[i + 1], f);
+            __syncthreads();
+            #pragma unroll
+            for (int r = 0; r < PPT; ++r)
+                if (ok[r]) par[r] ^= tile_parity(s_rec, s_v, nt, pt[r], f, st_fbp, st_fbe);
+            __syncthreads();
+        }
+        // XOR the partial parities into the output words (the block need not be word-aligned)
+        #pragma unroll
+        for (int r = 0; r < PPT; ++r) {
+            const long long cw = cb0 + (tid & ~31) + r * LG_THREADS;   // candidate of lane 0
+            const unsigned bits = __ballot_sync(FULL, ok[r] && par[r]);
+            if (lane == 0 && bits) {
+                const int sh = (int)(cw & 31);
+                atomicXor(a.out_bits + (cw >> 5), bits << sh);
+                if (sh) {
+                    const unsigned hi = bits >> (32 - sh);
+                    if (hi) atomicXor(a.out_bits + (cw >> 5) + 1, hi);
+                }
+            }
         }
         __syncthreads();
     }
@@ -324,48 +616,93 @@ __global__ void __launch_bounds__(FT_THREADS) k_pip_filtered(ClassifyArgs a, lon
         #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
             st_cand += __shfl_down_sync(FULL, st_cand, o);
-            st_rej += __shfl_down_sync(FULL, st_rej, o);
             st_fbp += __shfl_down_sync(FULL, st_fbp, o);
             st_fbe += __shfl_down_sync(FULL, st_fbe, o);
         }
         if (lane == 0) {
             if (st_cand) atomicAdd(a.stats + ST_CANDIDATES, st_cand);
-            if (st_rej) atomicAdd(a.stats + ST_BBOX_REJECTS, st_rej);
             if (st_fbp) atomicAdd(a.stats + ST_FALLBACK_POINTS, st_fbp);
             if (st_fbe) atomicAdd(a.stats + ST_FALLBACK_EDGES, st_fbe);
         }
     }
+    // the last CTA to finish empties the list for the next call
+    if (tid == 0) {
+        __threadfence();
+        if (atomicAdd(&ll->done, 1) == (int)gridDim.x - 1) {
+            ll->count = 0;
+            ll->cursor = 0;
+            ll->overflow = 0;
+            ll->done = 0;
+            __threadfence();
+        }
+    }
 }
 
-template <int PPT>
-static int launch_ppt(const ClassifyArgs &a, long long total_bits, int T, int grid, cudaStream_t stream)
+// =============================================================================================
+// launch
+// =============================================================================================
+
+template <typename K>
+static int ensure_smem(K kernel, size_t smem, size_t *configured)
 {
-    const size_t smem = filtered_smem_bytes(T);
-    static size_t configured[64] = {0};
     int dev = 0;
     cudaGetDevice(&dev);
     if (dev >= 0 && dev < 64 && configured[dev] < smem) {
-        cudaError_t e = cudaFuncSetAttribute(k_pip_filtered<PPT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smem);
+        cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return (int)e;
         configured[dev] = smem;
     }
-    k_pip_filtered<PPT><<<grid, FT_THREADS, smem, stream>>>(a, total_bits, T);
+    return 0;
+}
+
+template <bool DENSE>
+static int launch_poly_d(const ClassifyArgs &a, long long total_bits, LargeList *ll, int lcap, int n_sm,
+                         cudaStream_t stream)
+{
+    static size_t configured[64] = {0};
+    static int blocks_per_sm[64] = {0};
+    const size_t smem = sizeof(PolySmem);
+    int e = ensure_smem(k_pip_poly<DENSE>, smem, configured);
+    if (e) return e;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev >= 0 && dev < 64 && blocks_per_sm[dev] == 0) {
+        int nb = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_pip_poly<DENSE>, PM_THREADS, smem) != cudaSuccess)
+            nb = 1;
+        blocks_per_sm[dev] = std::max(nb, 1);
+    }
+    const int bps = (dev >= 0 && dev < 64) ? blocks_per_sm[dev] : 1;
+    const long long nchunk = ((long long)a.n_polys + PM_NP - 1) / PM_NP;
+    const int grid = (int)std::max(1LL, std::min((long long)n_sm * bps, nchunk));
+    k_pip_poly<DENSE><<<grid, PM_THREADS, smem, stream>>>(a, total_bits, ll, lcap);
     return (int)cudaGetLastError();
 }
 
-int launch_filtered(const ClassifyArgs &a, long long total_bits, const Tuning &t, int n_sm, cudaStream_t stream)
+template <int PPT>
+static int launch_large_ppt(const ClassifyArgs &a, long long total_bits, LargeList *ll, int lcap, int T, int grid,
+                            cudaStream_t stream)
 {
-    long long grid = (long long)n_sm * t.ctas_per_sm;
-    if (a.cand_offsets == nullptr) {
-        const long long ch = (long long)FT_THREADS * t.pts_per_thread;
-        grid = std::min(grid, (total_bits + ch - 1) / ch);
-    }
-    if (grid < 1) grid = 1;
+    static size_t configured[64] = {0};
+    const size_t smem = filtered_smem_bytes(T);
+    int e = ensure_smem(k_pip_large<PPT>, smem, configured);
+    if (e) return e;
+    const int ES = std::max(T, (16384 / T) * T);
+    k_pip_large<PPT><<<grid, LG_THREADS, smem, stream>>>(a, total_bits, ll, lcap, T, ES);
+    return (int)cudaGetLastError();
+}
+
+int launch_filtered(const ClassifyArgs &a, long long total_bits, const Tuning &t, int n_sm, LargeList *ll, int lcap,
+                    cudaStream_t stream)
+{
+    int e = a.cand_offsets ? launch_poly_d<false>(a, total_bits, ll, lcap, n_sm, stream)
+                           : launch_poly_d<true>(a, total_bits, ll, lcap, n_sm, stream);
+    if (e) return e;
+    const int grid = n_sm * t.ctas_per_sm;
     switch (t.pts_per_thread) {
-        case 1: return launch_ppt<1>(a, total_bits, t.edge_tile, (int)grid, stream);
-        case 2: return launch_ppt<2>(a, total_bits, t.edge_tile, (int)grid, stream);
-        default: return launch_ppt<4>(a, total_bits, t.edge_tile, (int)grid, stream);
+        case 1: return launch_large_ppt<1>(a, total_bits, ll, lcap, t.edge_tile, grid, stream);
+        case 4: return launch_large_ppt<4>(a, total_bits, ll, lcap, t.edge_tile, grid, stream);
+        default: return launch_large_ppt<2>(a, total_bits, ll, lcap, t.edge_tile, grid, stream);
     }
 }
 

@@ -9,16 +9,19 @@ namespace pipdev {
 
 struct ClassifyArgs;
 
-// Tuned shape of the filtered kernel.
+struct LargeList;
+
+// Tuned shape of pip_classify's two kernels.
 struct Tuning {
-    int edge_tile;       // edges staged in shared memory per pass
-    int pts_per_thread;  // candidates carried by each thread (1, 2, 4)
-    int ctas_per_sm;     // resident CTAs per SM of the persistent grid
+    int edge_tile;       // large-polygon kernel: edges staged in shared memory per pass
+    int pts_per_warp;    // batched kernel: candidates per warp group (64, 128, 256)
+    int ctas_per_sm;     // large-polygon kernel: resident CTAs per SM
+    int pts_per_thread;  // large-polygon kernel: candidates carried by each thread (1, 2, 4)
 };
 
 int launch_exact(const ClassifyArgs &a, long long total_bits, int grid, cudaStream_t stream);
-int launch_filtered(const ClassifyArgs &a, long long total_bits, const Tuning &t, int n_sm,
-                    cudaStream_t stream);
+int launch_filtered(const ClassifyArgs &a, long long total_bits, const Tuning &t, int n_sm, LargeList *ll,
+                    int lcap, cudaStream_t stream);
 size_t filtered_smem_bytes(int edge_tile);
 int launch_validate(const ClassifyArgs &a, long long n_verts, long long n_cand_ids, int *d_status, int grid,
                     cudaStream_t stream);

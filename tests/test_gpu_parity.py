@@ -152,7 +152,8 @@ def test_many_empty_polygons_in_one_chunk(api):
     check_full(api, make("sparse-csr", polys, pts, csr))
 
 
-@pytest.mark.parametrize("tuning", [(256, 1, 1), (512, 2, 2), (1024, 4, 2), (2048, 2, 3), (6144, 1, 1)])
+@pytest.mark.parametrize("tuning", [(256, 64, 1, 1), (512, 128, 2, 2), (1024, 256, 2, 4), (2048, 128, 3, 2),
+                                    (8192, 64, 1, 1)])
 def test_tuning_shapes(api, tuning):
     """Every tuned shape gives the same bits (small edge tiles force the streamed path)."""
     before = api.pip_get_tuning()
@@ -223,3 +224,66 @@ def test_binning_is_deterministic(api):
     co2, ids2 = api.bin_join(d["points"], d["poly_offsets"], d["verts"])
     torch.cuda.synchronize()
     assert torch.equal(co1, co2) and torch.equal(ids1, ids2)
+
+
+def _concat(ws, name):
+    """Concatenate CSR workloads (polygons, points and candidate lists) into one."""
+    pts, po, vs, co, ids = [], [0], [], [0], []
+    npts = nv = nc = 0
+    for w in ws:
+        pts.append(w.points)
+        vs.append(w.verts)
+        po += list(np.asarray(w.poly_offsets[1:], dtype=np.int64) + nv)
+        co += list(np.asarray(w.cand_offsets[1:], dtype=np.int64) + nc)
+        ids.append(w.cand_ids.astype(np.int64) + npts)
+        npts += w.n_points
+        nv += w.verts.shape[0]
+        nc += w.n_bits
+    return W.Workload(name, np.concatenate(pts), np.array(po, dtype=np.int32), np.concatenate(vs),
+                      np.array(co, dtype=np.int32), np.concatenate(ids).astype(np.int32))
+
+
+def test_small_and_large_polygons_interleaved(api):
+    """Output words shared by small polygons (batched kernel) and large ones (large-polygon
+    kernel, XOR into the same words); candidate blocks not aligned to words."""
+    parts = []
+    for i in range(6):
+        parts.append(W.footprints(seed=100 + i, n_polys=37 + 5 * i, pts_per_poly=3 + i))
+        parts.append(W.fractal(seed=200 + i, n_polys=1, m_lo=121 + 400 * i, m_hi=122 + 400 * i,
+                               n_points=700 + 131 * i, cell=100_000, grid=1))
+    check_full(api, _concat(parts, "mixed"))
+
+
+def test_large_list_overflow_scan_mode(api):
+    """More large polygons than the per-call list holds (65,536): the large-polygon kernel
+    falls back to scanning every polygon."""
+    rng = np.random.default_rng(41)
+    n = 66_000
+    m = 124
+    ang = np.sort(rng.uniform(0, 2 * np.pi, (n, m)), axis=1)
+    cx = rng.integers(-10**9, 10**9, n)[:, None]
+    cy = rng.integers(-10**9, 10**9, n)[:, None]
+    vx = (cx + 1000 * np.cos(ang)).astype(np.int64)
+    vy = (cy + 1000 * np.sin(ang)).astype(np.int64)
+    verts = np.stack([vx.ravel(), vy.ravel()], 1).astype(np.int32)
+    po = (np.arange(n + 1) * m).astype(np.int32)
+    pts = np.stack([np.concatenate([cx[:, 0], cx[:, 0] + 990]), np.concatenate([cy[:, 0], cy[:, 0]])], 1)
+    co = (np.arange(n + 1) * 2).astype(np.int32)
+    ids = np.stack([np.arange(n), np.arange(n) + n], 1).ravel().astype(np.int32)
+    w = W.Workload("overflow", pts.astype(np.int32), po, verts, co, ids)
+    check_full(api, w)
+
+
+def test_repeated_calls_and_streams(api):
+    """The large-polygon list empties itself: repeated calls, and calls on a second stream."""
+    w = W.fractal(seed=51, n_polys=3, m_lo=2000, m_hi=5000, n_points=20_000, cell=300_000, grid=2)
+    want = oracle.classify(w.points, w.poly_offsets, w.verts, w.cand_offsets, w.cand_ids)
+    d = api.to_device(w)
+    s2 = torch.cuda.Stream()
+    for i in range(4):
+        st = s2 if i % 2 else torch.cuda.current_stream()
+        with torch.cuda.stream(st):
+            out = api.pip_classify(d["points"], d["poly_offsets"], d["verts"], d["cand_offsets"], d["cand_ids"],
+                                   n_cands=w.n_bits)
+        st.synchronize()
+        assert_same(out.cpu().numpy().view(np.uint32)[:w.n_words], want, w.n_bits, f"call {i}")
