@@ -101,6 +101,30 @@ int pip_classify_exact(const int32_t *points, int64_t n_points,
                        uint32_t *out_bits, void *stream);
 
 /*
+ * pip_classify_noalloc -- pip_classify for callers that cannot allocate device memory (the
+ * paper has no counterpart).  pip_classify allocates, on its first call on each stream, the
+ * device list that hands large polygons to its second kernel (and, once per device, its
+ * statistics counters).  Callers that must not trigger cudaMalloc -- code running during CUDA
+ * graph capture, applications that manage all device memory through their own allocator or a
+ * fixed budget, paths that cannot afford cudaMalloc's implicit synchronisation -- can call
+ * this variant instead: same arguments, same bits, same kernels, but the list lives in a
+ * fixed array inside the library's device image (512 KiB per device, held until the process
+ * exits), so no call allocates.
+ *   Limit: n_polys <= PIP_NOALLOC_MAX_POLYS, else PIP_ERR_TOO_LARGE (the array holds one list
+ *   entry per polygon of the call).
+ *   The first call on a device looks up the array's device address (cudaGetSymbolAddress);
+ *   make that first call before any stream capture that includes this entry point.
+ *   Every call shares the one array and clears its header on `stream` first; calls whose
+ *   work overlaps on the GPU (different streams, or different host threads) race on it and
+ *   must be serialised by the caller.  pip_get_stats counters are not updated.
+ */
+#define PIP_NOALLOC_MAX_POLYS 65536
+int pip_classify_noalloc(const int32_t *points, int64_t n_points,
+                         const int32_t *poly_offsets, const int32_t *verts, int32_t n_polys,
+                         const int32_t *cand_offsets, const int32_t *cand_ids,
+                         uint32_t *out_bits, void *stream);
+
+/*
  * Uniform-grid binning (not in the paper; it builds the candidate CSR of a spatial join):
  * candidates of polygon k = every point inside k's CLOSED bounding box, listed in a fixed
  * order (grid cells row-major over the box, ascending point id within a cell), so that

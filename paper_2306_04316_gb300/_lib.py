@@ -21,6 +21,7 @@ PIP_ERR_TOO_LARGE = -4
 PIP_ERR_WORKSPACE = -5
 PIP_ERR_CUDA = -6
 PIP_ERR_INVALID = -7
+PIP_NOALLOC_MAX_POLYS = 65536
 
 
 class PipStats(ctypes.Structure):
@@ -51,6 +52,7 @@ _I32 = ctypes.c_int32
 _SIGS = {
     "pip_classify": ([_P, _I64, _P, _P, _I32, _P, _P, _P, _P], ctypes.c_int),
     "pip_classify_exact": ([_P, _I64, _P, _P, _I32, _P, _P, _P, _P], ctypes.c_int),
+    "pip_classify_noalloc": ([_P, _I64, _P, _P, _I32, _P, _P, _P, _P], ctypes.c_int),
     "pip_bin_workspace_bytes": ([_I64, _I32], ctypes.c_size_t),
     "pip_bin_count": ([_P, _I64, _P, _P, _I32, _I32, _P, ctypes.c_size_t, _P, _P, _P], ctypes.c_int),
     "pip_bin_fill": ([_P, _I64, _P, _P, _I32, _P, ctypes.c_size_t, _P, _P, _I64, _P, _P], ctypes.c_int),

@@ -14,7 +14,7 @@ import torch
 
 from . import _lib
 
-__all__ = ["pip_classify", "pip_classify_exact", "pip_bin_count", "pip_bin_fill", "bin_join",
+__all__ = ["pip_classify", "pip_classify_exact", "pip_classify_noalloc", "pip_bin_count", "pip_bin_fill", "bin_join",
            "pip_set_tuning", "pip_get_tuning", "pip_get_stats", "pip_reset_stats", "pip_validate",
            "out_words", "to_device"]
 
@@ -88,6 +88,14 @@ def pip_classify_exact(points, poly_offsets, verts, cand_offsets=None, cand_ids=
                        n_cands=None, stream=None):
     """Plain exact integer classification (``pip_classify_exact``); returns out_bits."""
     return _classify("pip_classify_exact", points, poly_offsets, verts, cand_offsets, cand_ids,
+                     out, n_cands, stream)
+
+
+def pip_classify_noalloc(points, poly_offsets, verts, cand_offsets=None, cand_ids=None, out=None,
+                         n_cands=None, stream=None):
+    """``pip_classify`` for callers that cannot allocate device memory (``out`` is still needed:
+    pass it, or let this wrapper allocate it); at most PIP_NOALLOC_MAX_POLYS polygons."""
+    return _classify("pip_classify_noalloc", points, poly_offsets, verts, cand_offsets, cand_ids,
                      out, n_cands, stream)
 
 

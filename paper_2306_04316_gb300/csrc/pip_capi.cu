@@ -130,6 +130,10 @@ ClassifyArgs make_args(const int32_t *points, int64_t n_points, const int32_t *p
 
 }  // namespace
 
+namespace pipdev {
+Tuning current_tuning() { return Tuning{g_edge_tile.load(), g_ppw.load(), g_ctas.load(), g_ppt.load()}; }
+}  // namespace pipdev
+
 extern "C" {
 
 int pip_classify(const int32_t *points, int64_t n_points, const int32_t *poly_offsets,

@@ -23,6 +23,7 @@ int launch_exact(const ClassifyArgs &a, long long total_bits, int grid, cudaStre
 int launch_filtered(const ClassifyArgs &a, long long total_bits, const Tuning &t, int n_sm, LargeList *ll,
                     int lcap, cudaStream_t stream);
 size_t filtered_smem_bytes(int edge_tile);
+Tuning current_tuning();   // the values set by pip_set_tuning
 int launch_validate(const ClassifyArgs &a, long long n_verts, long long n_cand_ids, int *d_status, int grid,
                     cudaStream_t stream);
 
