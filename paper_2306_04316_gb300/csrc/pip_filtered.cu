@@ -30,17 +30,21 @@
 //
 // Two kernels, launched back to back on the caller's stream:
 //
-// k_pip_poly -- polygon-major.  A CTA takes a chunk of 128 consecutive polygons, so that every
-//   array it reads is one contiguous range: the chunk's vertex and candidate offsets, its
-//   vertices and its candidate ids; only the candidate points are gathered (cp.async into
-//   shared memory).  It stages runs of whole polygons (up to 1,024 vertices per pass), computes
-//   each polygon's bounding box, frame and bound (thread per polygon) and the edge records
-//   (thread per edge), then classifies the run's candidates (thread per candidate, passes of
-//   2,048) against the records in shared memory.  Results are packed by warp ballots into
-//   shared words and written out; the first and last word of a pass may be shared with a
-//   neighbouring chunk, so those are written with a masked AND/OR pair that sets exactly the
-//   pass's own bits (no zero-fill pass is needed).  Polygons with more than 1,024 vertices or
-//   more than 2^18 (candidate, edge) pairs get bit 0 here and go on a device-side list.
+// k_pip_pipe -- polygon-major, producer/consumer.  A CTA takes chunks of 128 consecutive
+//   polygons, so that every array it reads is one contiguous range: the chunk's vertex and
+//   candidate offsets, its vertices and its candidate ids; only the candidate points are
+//   gathered.  One producer warp cuts each chunk into passes (runs of whole polygons with at
+//   most 1,024 vertices and 1,024 candidates) and stages a pass's offsets, vertices and
+//   gathered points into one of two shared-memory stages with cp.async, while seven consumer
+//   warps classify the previous pass: bounding box, frame and bound per polygon, FP32 edge
+//   records per edge, then a queue of the candidates inside their polygon's box (polygons of
+//   at most 8 edges from the front, longer ones from the back, so that a warp's lanes walk
+//   similar edge counts) and the edge loop.  Named barriers hand stages back and forth.
+//   Results are packed into shared words and written out; the first and last word of a pass
+//   may be shared with a neighbouring pass, so those are written with a masked AND/OR pair
+//   that sets exactly the pass's own bits (no zero-fill pass is needed).  Polygons with more
+//   than 1,024 vertices or more than 2^18 (candidate, edge) pairs get bit 0 here and go on a
+//   device-side list.
 //
 // k_pip_large -- the listed polygons.  Work items (polygon, block of 256*PPT candidates,
 //   slice of edges) are taken from the list by atomic counters; the CTA streams the slice
@@ -135,7 +139,7 @@ __device__ __noinline__ int exact_parity(const int2 *v, int e0, int e1, bool wra
 }
 
 // =============================================================================================
-// k_pip_poly
+// k_pip_pipe -- small polygons, polygon-major, producer/consumer
 // =============================================================================================
 
 // Bound factor of the FP32 records: rounding the four record inputs, the product Y d_x and the
@@ -143,29 +147,50 @@ __device__ __noinline__ int exact_parity(const int2 *v, int e0, int e1, bool wra
 // 5u|X d_y| + 6u|Y d_x| + 4u|P_x d_y| + 3u|P_y d_x| (+ O(u^2)) <= 12u (M_x H + M_y W), with H, W
 // the polygon's height and width (>= |d_y|, |d_x| of every edge).
 constexpr float PM_BOUND_K = 7.748603820800781e-07f;     // 13 * 2^-24 (exact in FP32)
-constexpr int PM_THREADS = 256;
-constexpr int PM_NP = 128;          // polygons per chunk
+constexpr int PM_THREADS = 256;     // warps 0-6 consume, warp 7 produces
+constexpr int PM_CONS = 224;
+constexpr int PM_NP = 128;          // polygons per chunk (and at most per pass)
 constexpr int PM_TV = 1024;         // staged vertices per pass
-constexpr int PM_TC = 2048;         // staged candidates per pass
+constexpr int PM_TC = 1024;         // staged candidates per pass
+constexpr int PM_SHORT = 8;         // polygons of at most this many edges share warps
 constexpr int PM_LARGE_M = 1024;    // polygons above this many vertices go to k_pip_large
 constexpr long long PM_LARGE_W = 1LL << 18;   // ... and those with more (candidates x vertices)
+// named barriers (0 is __syncthreads)
+constexpr int BAR_CONS = 1, BAR_FULL = 2, BAR_EMPTY = 4;
 
-struct __align__(16) PolySmem {
-    float4 rec[PM_TV];              // edge records
-    int2 v[PM_TV + 1];              // raw vertices
-    int2 pts[PM_TC];                // candidate points
-    int4 pbox[PM_NP];               // bounding box per chunk polygon
-    int4 pfr[PM_NP];                // frame: ox, oy, bound (float bits), wide
-    unsigned short vp[PM_TV];       // vertex -> chunk polygon
-    unsigned short cp[PM_TC];       // candidate -> chunk polygon (0xffff: padding)
-    unsigned short queue[PM_TC];    // candidates inside their polygon's box
-    int ids[PM_TC];                 // candidate ids of the pass (CSR)
-    int co32[PM_NP + 1];            // candidate offsets as loaded (CSR)
-    unsigned words[PM_TC / 32 + 2]; // result bits of the candidate pass
-    long long co[PM_NP + 1];        // candidate offsets of the chunk's polygons
-    int po[PM_NP + 1];              // vertex offsets
-    unsigned lg[PM_NP / 32];        // bit q: chunk polygon q goes to k_pip_large
-    int run_end, nq;
+__device__ __forceinline__ void bar_sync(int id, int n) { asm volatile("bar.sync %0, %1;\n" ::"r"(id), "r"(n) : "memory"); }
+__device__ __forceinline__ void bar_arrive(int id, int n) { asm volatile("bar.arrive %0, %1;\n" ::"r"(id), "r"(n) : "memory"); }
+
+template <typename CI>
+struct __align__(16) PipeStage {
+    int2 v[PM_TV + 2];              // the pass's vertices
+    int2 pts[PM_TC];                // the pass's candidate points
+    CI co[PM_NP + 1];               // candidate offsets of the pass's polygons
+    int po[PM_NP + 1];              // vertex offsets (global)
+    int kind;                       // 0 end, 1 run of small polygons, 2 one large polygon
+    int kg0;                        // global index of the pass's polygon 0
+    int np;                         // polygons in the pass
+    int nc;                         // candidates [cb0, cb0 + nc)
+    CI cb0;
+};
+
+template <typename CI>
+struct __align__(16) PipeSmem {
+    PipeStage<CI> st[2];
+    // consumer-private
+    float4 rec[PM_TV];
+    int4 pbox[PM_NP];
+    int4 pfr[PM_NP];                // ox, oy, bound (float bits), wide
+    unsigned short vp[PM_TV];
+    unsigned short cp[PM_TC];
+    unsigned short queue[PM_TC];
+    unsigned words[PM_TC / 32 + 2];
+    int qfront, qback;
+    // producer-private
+    int ids[PM_TC];
+    int ppo[PM_NP + 1];
+    CI pco[PM_NP + 1];
+    unsigned plg[PM_NP / 32];
 };
 
 __device__ __forceinline__ bool pm_is_large(long long m, long long n)
@@ -184,238 +209,292 @@ __device__ __forceinline__ void masked_store(uint32_t *word, unsigned mask, unsi
     }
 }
 
+__device__ __forceinline__ unsigned range_mask(int lo, int hi)   // bits [lo, hi), 0 <= lo <= hi <= 32
+{
+    return (hi >= 32 ? 0xffffffffu : ((1u << hi) - 1u)) & ~((1u << lo) - 1u);
+}
+
 template <bool DENSE>
-__global__ void __launch_bounds__(PM_THREADS, 4) k_pip_poly(ClassifyArgs a, long long total_bits, LargeList *ll,
+__global__ void __launch_bounds__(PM_THREADS, 3) k_pip_pipe(ClassifyArgs a, long long total_bits, LargeList *ll,
                                                             int lcap)
 {
     using CI = typename std::conditional<DENSE, long long, int>::type;
     extern __shared__ __align__(16) unsigned char dsm[];
-    PolySmem &sm = *reinterpret_cast<PolySmem *>(dsm);
+    PipeSmem<CI> &sm = *reinterpret_cast<PipeSmem<CI> *>(dsm);
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const int P = a.n_polys;
     const CI W32 = (CI)(a.words_per_poly * 32);
     const CI NPTS = (CI)a.n_points;
     const int nchunk = (P + PM_NP - 1) / PM_NP;
-    unsigned st_cand = 0, st_rej = 0, st_fbp = 0;
-    if (!DENSE && blockIdx.x == 0 && tid == 0 && P > 0) {
-        // bits past the last candidate in the final word are 0
-        const long long C = __ldg(a.cand_offsets + P);
-        if (C & 31) masked_store(a.out_bits + (C >> 5), ~((1u << (C & 31)) - 1u), 0u);
-    }
 
-    for (int ch = blockIdx.x; ch < nchunk; ch += gridDim.x) {
-        const int k0 = ch * PM_NP;
-        const int np = min(PM_NP, P - k0);
-        if (tid < PM_NP / 32) sm.lg[tid] = 0;
-        for (int t = tid; t <= np; t += PM_THREADS) {
-            cp_async4(&sm.po[t], a.poly_offsets + k0 + t);
-            if (!DENSE) cp_async4(&sm.co32[t], a.cand_offsets + k0 + t);
+    if (wid == 7) {
+        // ================================ producer ================================
+        if (!DENSE && blockIdx.x == 0 && lane == 0 && P > 0) {
+            // bits past the last candidate in the final word are 0
+            const long long C = __ldg(a.cand_offsets + P);
+            if (C & 31) masked_store(a.out_bits + (C >> 5), ~((1u << (C & 31)) - 1u), 0u);
         }
-        cp_async_commit();
-        cp_async_wait_all();
-        __syncthreads();
-        for (int t = tid; t <= np; t += PM_THREADS)
-            sm.co[t] = DENSE ? (long long)(k0 + t) * W32 : (long long)sm.co32[t];
-        __syncthreads();
-        for (int q = tid; q < np; q += PM_THREADS) {
-            const long long n = DENSE ? min((long long)NPTS, (long long)W32) : sm.co[q + 1] - sm.co[q];
-            if (pm_is_large(sm.po[q + 1] - sm.po[q], n)) atomicOr(&sm.lg[q >> 5], 1u << (q & 31));
-        }
-        int pa = 0;
-        while (pa < np) {
-            __syncthreads();
-            // ---- warp 0: the next run of small polygons whose vertices fit one pass (or one
-            //      large polygon); lane l tests run end pa + 1 + l, ...
-            if (wid == 0) {
-                const bool large0 = (sm.lg[pa >> 5] >> (pa & 31)) & 1u;
-                int pb = pa + 1;
-                if (!large0) {
-                    for (int base = pa + 1; base <= np; base += 32) {
-                        const int q = base + lane;   // candidate end: polygons [pa, q)
-                        const bool ok = q <= np && sm.po[q] - sm.po[pa] <= PM_TV &&
-                                        !((sm.lg[(q - 1) >> 5] >> ((q - 1) & 31)) & 1u);
-                        const unsigned bm = __ballot_sync(FULL, ok);
-                        // ok is a prefix property (monotone) up to the first failure
-                        const unsigned run = ~bm ? (__ffs(~bm) - 1) : 32;
-                        pb = base + (int)run - 1;
-                        if (run < 32) break;
-                    }
-                    pb = max(pb, pa + 1);
-                }
-                if (lane == 0) sm.run_end = large0 ? -(pa + 1) : pb;
+        int j = 0;   // pass counter
+        // claim stage j & 1 (after the consumers released pass j - 2)
+        auto begin = [&]() -> PipeStage<CI> & {
+            if (j >= 2) bar_sync(BAR_EMPTY + (j & 1), PM_THREADS);
+            return sm.st[j & 1];
+        };
+        auto publish = [&]() {
+            cp_async_wait_all();
+            __threadfence_block();
+            __syncwarp();
+            bar_arrive(BAR_FULL + (j & 1), PM_THREADS);
+            ++j;
+        };
+        // fill a stage with polygons [p, q) of the chunk and candidates [cb0, cb0 + nc)
+        auto fill = [&](PipeStage<CI> &S, int k0, int p, int q, int kind, CI cb0, int nc) {
+            if (lane == 0) { S.kind = kind; S.kg0 = k0 + p; S.np = q - p; S.nc = nc; S.cb0 = cb0; }
+            for (int t = lane; t <= q - p; t += 32) { S.po[t] = sm.ppo[p + t]; S.co[t] = sm.pco[p + t]; }
+            if (kind != 1) return;
+            const int vb = sm.ppo[p], nv = sm.ppo[q] - vb;
+            for (int i = lane; i < nv; i += 32) cp_async8(&S.v[i], a.verts + vb + i);
+            if (!DENSE) {
+                for (int i = lane; i < nc; i += 32) cp_async4(&sm.ids[i], a.cand_ids + cb0 + i);
+                cp_async_commit();
+                cp_async_wait_all();
+                __syncwarp();
             }
-            __syncthreads();
-            const bool large = sm.run_end < 0;
-            const int pb = large ? pa + 1 : sm.run_end;
-            const CI cbeg = (CI)sm.co[pa], cfin = (CI)sm.co[pb];
-            const int vbase = sm.po[pa];
-            if (large) {
-                // bits 0 here (k_pip_large XORs the parities in later); the list gets the polygon
-                if (tid == 0 && cfin > cbeg && NPTS > 0) {
-                    const int idx = atomicAdd(&ll->count, 1);
-                    if (idx < lcap) {
-                        large_entries(ll)[idx] = k0 + pa;
-                        large_taken(ll, lcap)[idx] = 0;
-                    } else {
-                        atomicExch(&ll->overflow, 1);
-                    }
+            for (int i = lane; i < nc; i += 32) {
+                CI pid;
+                if (DENSE) {
+                    const CI c = cb0 + i;
+                    pid = c - (c / W32) * W32;
+                } else {
+                    pid = sm.ids[i];
                 }
-                const CI w0 = cbeg >> 5, w1 = (cfin + 31) >> 5;
-                for (CI wd = w0 + tid; wd < w1; wd += PM_THREADS) {
-                    const int lo = (int)(max(cbeg, wd * 32) - wd * 32), hi = (int)(min(cfin, wd * 32 + 32) - wd * 32);
-                    const unsigned mask = (hi >= 32 ? 0xffffffffu : ((1u << hi) - 1u)) & ~((1u << lo) - 1u);
-                    masked_store(a.out_bits + wd, mask, 0u);
-                }
-                pa = pb;
-                continue;
+                if (pid < NPTS) cp_async8(&S.pts[i], a.points + pid);
             }
-            // ---- stage the run's vertices; bounding boxes and frames, one thread per polygon
-            const int nv = sm.po[pb] - vbase;
-            for (int i = tid; i < nv; i += PM_THREADS) cp_async8(&sm.v[i], a.verts + vbase + i);
             cp_async_commit();
-            const int nc0 = (int)min((CI)PM_TC, cfin - cbeg);
-            if (!DENSE)   // the first pass's candidate ids travel with the vertices
-                for (int i = tid; i < nc0; i += PM_THREADS) cp_async4(&sm.ids[i], a.cand_ids + cbeg + i);
+        };
+        for (int ch = blockIdx.x; ch < nchunk; ch += gridDim.x) {
+            const int k0 = ch * PM_NP;
+            const int np = min(PM_NP, P - k0);
+            for (int t = lane; t <= np; t += 32) {
+                cp_async4(&sm.ppo[t], a.poly_offsets + k0 + t);
+                if (!DENSE) cp_async4(&sm.pco[t], a.cand_offsets + k0 + t);
+            }
             cp_async_commit();
             cp_async_wait_all();
-            __syncthreads();
-            for (int q = pa + tid; q < pb; q += PM_THREADS) {
-                const int e0 = sm.po[q] - vbase, e1 = sm.po[q + 1] - vbase;
-                int x0 = INT_MAX, y0 = INT_MAX, x1 = INT_MIN, y1 = INT_MIN;
-                for (int i = e0; i < e1; ++i) {
-                    const int2 v = sm.v[i];
-                    x0 = min(x0, v.x); y0 = min(y0, v.y); x1 = max(x1, v.x); y1 = max(y1, v.y);
-                    sm.vp[i] = (unsigned short)q;
+            __syncwarp();
+            if (DENSE)
+                for (int t = lane; t <= np; t += 32) sm.pco[t] = (CI)(k0 + t) * W32;
+            __syncwarp();
+            #pragma unroll
+            for (int b = 0; b < PM_NP / 32; ++b) {
+                const int q = 32 * b + lane;
+                bool lg = false;
+                if (q < np) {
+                    const long long n = DENSE ? min((long long)NPTS, (long long)W32) : (long long)(sm.pco[q + 1] - sm.pco[q]);
+                    lg = pm_is_large(sm.ppo[q + 1] - sm.ppo[q], n);
                 }
-                const unsigned W = (unsigned)x1 - (unsigned)x0, H = (unsigned)y1 - (unsigned)y0;
-                const unsigned Mx = W - (W >> 1), My = H - (H >> 1);
-                const float B = __fmul_ru(PM_BOUND_K, __fadd_ru(__fmul_ru(__uint2float_ru(Mx), __uint2float_ru(H)),
-                                                                 __fmul_ru(__uint2float_ru(My), __uint2float_ru(W))));
-                sm.pfr[q] = make_int4(x0 + (int)(W >> 1), y0 + (int)(H >> 1), __float_as_int(B),
-                                      (Mx >= (1u << 30)) | (My >= (1u << 30)));
-                sm.pbox[q] = make_int4(x0, y0, x1, y1);
+                const unsigned m = __ballot_sync(FULL, lg);
+                if (lane == 0) sm.plg[b] = m;
             }
-            __syncthreads();
-            // ---- edge records, one thread per edge (FP32 unless the frame is 2^30 wide)
-            for (int i = tid; i < nv; i += PM_THREADS) {
-                const int q = sm.vp[i];
-                const int nx = (i + 1 == sm.po[q + 1] - vbase) ? sm.po[q] - vbase : i + 1;
-                const int2 ri = sm.v[i], rj = sm.v[nx];
-                const int4 f = sm.pfr[q];
-                float4 rec;
-                if (!f.w) {
-                    const int dx = rj.x - ri.x, dy = rj.y - ri.y;
-                    const float fdx = __int2float_rn(dx), fdy = __int2float_rn(dy);
-                    const float X = __int2float_rn(ri.x - f.x), Y = __int2float_rn(ri.y - f.y);
-                    const float c = __fmaf_rn(X, fdy, -__fmul_rn(Y, fdx));
-                    rec = dy > 0 ? make_float4(c, fdy, fdx, __int_as_float(rj.y))
-                                 : make_float4(-c, -fdy, -fdx, __int_as_float(rj.y));
-                } else {
-                    rec = wide_record(ri, rj, f.x, f.y);
+            __syncwarp();
+            int p = 0;
+            while (p < np) {
+                if ((sm.plg[p >> 5] >> (p & 31)) & 1u) {
+                    PipeStage<CI> &S = begin();
+                    fill(S, k0, p, p + 1, 2, (CI)sm.pco[p], 0);
+                    publish();
+                    ++p;
+                    continue;
                 }
-                sm.rec[i] = rec;
+                // run [p, q): small polygons, vertices <= PM_TV, candidates <= PM_TC
+                int q = p + 1;
+                for (int base = p + 1; base <= np; base += 32) {
+                    const int e = base + lane;
+                    const bool ok = e <= np && sm.ppo[e] - sm.ppo[p] <= PM_TV &&
+                                    (long long)(sm.pco[e] - sm.pco[p]) <= PM_TC &&
+                                    !((sm.plg[(e - 1) >> 5] >> ((e - 1) & 31)) & 1u);
+                    const unsigned bm = __ballot_sync(FULL, ok);
+                    const int run = bm == FULL ? 32 : __ffs(~bm) - 1;
+                    if (run > 0) q = base + run - 1;
+                    if (run < 32) break;
+                }
+                q = max(q, p + 1);
+                const CI c0 = (CI)sm.pco[p], c1 = (CI)sm.pco[q];
+                if (c1 - c0 <= PM_TC) {
+                    PipeStage<CI> &S = begin();
+                    fill(S, k0, p, q, 1, c0, (int)(c1 - c0));
+                    publish();
+                } else {   // one polygon with more candidates than a pass holds
+                    for (CI cb = c0; cb < c1; cb += PM_TC) {
+                        PipeStage<CI> &S = begin();
+                        fill(S, k0, p, p + 1, 1, cb, (int)min((CI)PM_TC, c1 - cb));
+                        publish();
+                    }
+                }
+                p = q;
             }
-            // ---- the run's candidates, in passes of PM_TC
-            for (CI cb0 = cbeg; cb0 < cfin; cb0 += PM_TC) {
-                const int nc = (int)min((CI)PM_TC, cfin - cb0);
-                // points: cp.async gathers into shared memory (ids of later passes staged first)
-                if (!DENSE && cb0 != cbeg) {
-                    __syncthreads();
-                    for (int i = tid; i < nc; i += PM_THREADS) cp_async4(&sm.ids[i], a.cand_ids + cb0 + i);
-                    cp_async_commit();
-                    cp_async_wait_all();
-                    __syncthreads();
-                }
-                for (int i = tid; i < nc; i += PM_THREADS) {
-                    const CI c = cb0 + i;
-                    CI pid;
-                    if (DENSE) pid = c - (c / W32) * W32;
-                    else pid = sm.ids[i];
-                    if (pid < NPTS) cp_async8(&sm.pts[i], a.points + pid);
-                }
-                cp_async_commit();
-                // candidate -> polygon, one thread per polygon
-                for (int q = pa + tid; q < pb; q += PM_THREADS) {
-                    const int s0 = (int)(max((CI)sm.co[q], cb0) - cb0);
-                    const int s1 = (int)(min((CI)sm.co[q + 1], cb0 + nc) - cb0);
-                    int s1v = s1;
-                    if (DENSE) s1v = (int)max((CI)s0, min((CI)s1 + cb0, (CI)sm.co[q] + NPTS) - cb0);
-                    for (int s = s0; s < s1v; ++s) sm.cp[s] = (unsigned short)q;
-                    for (int s = s1v; s < s1; ++s) sm.cp[s] = 0xffff;   // dense padding
-                }
-                for (int t = tid; t < PM_TC / 32 + 2; t += PM_THREADS) sm.words[t] = 0;
-                if (tid == 0) sm.nq = 0;
-                cp_async_wait_all();
-                __syncthreads();
-                // queue the candidates inside their polygon's box
-                for (int i0 = 0; i0 < nc; i0 += PM_THREADS) {
-                    const int i = i0 + tid;
-                    bool q = false;
-                    if (i < nc) {
-                        const int pq = sm.cp[i];
-                        if (pq != 0xffff) {
-                            const int2 p = sm.pts[i];
-                            const int4 b = sm.pbox[pq];
-                            q = p.x >= b.x && p.x <= b.z && p.y >= b.y && p.y <= b.w;
-                            ++st_cand;
-                        }
-                    }
-                    const unsigned qm = __ballot_sync(FULL, q);
-                    int base = 0;
-                    if (lane == 0 && qm) base = atomicAdd(&sm.nq, __popc(qm));
-                    base = __shfl_sync(FULL, base, 0);
-                    if (q) sm.queue[base + __popc(qm & ((1u << lane) - 1u))] = (unsigned short)i;
-                }
-                __syncthreads();
-                const int nq = sm.nq;
-                st_rej -= (unsigned)(tid == 0 ? nq : 0);
-                // the edge loop, one queued candidate per thread
-                const int sh = (int)(cb0 & 31);   // bit of candidate cb0 within its word
-                for (int qi = tid; qi < nq; qi += PM_THREADS) {
-                    const int i = sm.queue[qi];
-                    const int pq = sm.cp[i];
-                    const int2 p = sm.pts[i];
-                    const int4 f = sm.pfr[pq];
-                    const int e0 = sm.po[pq] - vbase, e1 = sm.po[pq + 1] - vbase;
-                    const float B = __int_as_float(f.z);
-                    const float Px = __int2float_rn(p.x - f.x), Py = __int2float_rn(p.y - f.y);
-                    bool sp = sm.v[e0].y > p.y;
-                    int parity = 0;
-                    bool unc = false;
-                    #pragma unroll 2
-                    for (int e = e0; e < e1; ++e) {
-                        const float4 q4 = sm.rec[e];
-                        const bool sn = __float_as_int(q4.w) > p.y;
-                        const bool st = sn != sp;
-                        sp = sn;
-                        float t = __fmaf_rn(-Px, q4.y, q4.x);
-                        t = __fmaf_rn(Py, q4.z, t);
-                        parity ^= (int)(st & (t > 0.f));
-                        unc |= st & (fabsf(t) <= B);
-                    }
-                    if (unc) {
-                        ++st_fbp;
-                        parity = exact_parity(sm.v, e0, e1, true, p);
-                    }
-                    if (parity) {
-                        const int b = sh + i;
-                        atomicOr(&sm.words[b >> 5], 1u << (b & 31));
-                    }
-                }
-                __syncthreads();
-                // write the pass's words: bits [sh, sh + nc) of words cb0 >> 5 ...
-                const int nwd = (sh + nc + 31) >> 5;
-                for (int t = tid; t < nwd; t += PM_THREADS) {
-                    const int lo = t == 0 ? sh : 0;
-                    const int hi = min(32, sh + nc - 32 * t);
-                    const unsigned mask = (hi >= 32 ? 0xffffffffu : ((1u << hi) - 1u)) & ~((1u << lo) - 1u);
-                    masked_store(a.out_bits + (cb0 >> 5) + t, mask, sm.words[t]);
-                }
-                __syncthreads();
-            }
-            pa = pb;
         }
-        __syncthreads();
+        {
+            PipeStage<CI> &S = begin();
+            if (lane == 0) S.kind = 0;
+            publish();
+        }
+        // the consumers' release of the last real pass (j - 2 after the end marker's ++j)
+        if (j >= 2) bar_sync(BAR_EMPTY + (j & 1), PM_THREADS);
+        return;
+    }
+
+    // ================================ consumers ================================
+    unsigned st_cand = 0, st_rej = 0, st_fbp = 0;
+    for (int j = 0;; ++j) {
+        bar_sync(BAR_FULL + (j & 1), PM_THREADS);
+        PipeStage<CI> &S = sm.st[j & 1];
+        const int kind = S.kind;
+        if (kind == 0) break;
+        const int np = S.np, nc = S.nc;
+        const CI cb0 = S.cb0;
+        if (kind == 2) {
+            // bits 0 here (k_pip_large XORs the parities in later); the list gets the polygon
+            const CI cbeg = S.co[0], cfin = S.co[1];
+            if (tid == 0 && cfin > cbeg && NPTS > 0) {
+                const int idx = atomicAdd(&ll->count, 1);
+                if (idx < lcap) {
+                    large_entries(ll)[idx] = S.kg0;
+                    large_taken(ll, lcap)[idx] = 0;
+                } else {
+                    atomicExch(&ll->overflow, 1);
+                }
+            }
+            const CI w0 = cbeg >> 5, w1 = (cfin + 31) >> 5;
+            for (CI wd = w0 + tid; wd < w1; wd += PM_CONS) {
+                const int lo = (int)(max(cbeg, wd * 32) - wd * 32), hi = (int)(min(cfin, wd * 32 + 32) - wd * 32);
+                masked_store(a.out_bits + wd, range_mask(lo, hi), 0u);
+            }
+            __threadfence_block();
+            bar_arrive(BAR_EMPTY + (j & 1), PM_THREADS);
+            continue;
+        }
+        const int vbase = S.po[0];
+        const int nv = S.po[np] - vbase;
+        // ---- bounding boxes and frames, one thread per polygon
+        for (int q = tid; q < np; q += PM_CONS) {
+            const int e0 = S.po[q] - vbase, e1 = S.po[q + 1] - vbase;
+            int x0 = INT_MAX, y0 = INT_MAX, x1 = INT_MIN, y1 = INT_MIN;
+            for (int i = e0; i < e1; ++i) {
+                const int2 v = S.v[i];
+                x0 = min(x0, v.x); y0 = min(y0, v.y); x1 = max(x1, v.x); y1 = max(y1, v.y);
+                sm.vp[i] = (unsigned short)q;
+            }
+            const unsigned W = (unsigned)x1 - (unsigned)x0, H = (unsigned)y1 - (unsigned)y0;
+            const unsigned Mx = W - (W >> 1), My = H - (H >> 1);
+            const float B = __fmul_ru(PM_BOUND_K, __fadd_ru(__fmul_ru(__uint2float_ru(Mx), __uint2float_ru(H)),
+                                                             __fmul_ru(__uint2float_ru(My), __uint2float_ru(W))));
+            sm.pfr[q] = make_int4(x0 + (int)(W >> 1), y0 + (int)(H >> 1), __float_as_int(B),
+                                  (Mx >= (1u << 30)) | (My >= (1u << 30)));
+            sm.pbox[q] = make_int4(x0, y0, x1, y1);
+            // candidate slots of this polygon in the pass
+            const int s0 = (int)(max(S.co[q], cb0) - cb0);
+            const int s1 = (int)(min(S.co[q + 1], cb0 + (CI)nc) - cb0);
+            int s1v = s1;
+            if (DENSE) s1v = (int)max((CI)s0, min((CI)s1 + cb0, S.co[q] + NPTS) - cb0);
+            for (int s = s0; s < s1v; ++s) sm.cp[s] = (unsigned short)q;
+            for (int s = s1v; s < s1; ++s) sm.cp[s] = 0xffff;   // dense padding
+        }
+        for (int t = tid; t < PM_TC / 32 + 2; t += PM_CONS) sm.words[t] = 0;
+        if (tid == 0) { sm.qfront = 0; sm.qback = PM_TC; }
+        bar_sync(BAR_CONS, PM_CONS);
+        // ---- edge records, one thread per edge (FP32 unless the frame is 2^30 wide)
+        for (int i = tid; i < nv; i += PM_CONS) {
+            const int q = sm.vp[i];
+            const int nx = (i + 1 == S.po[q + 1] - vbase) ? S.po[q] - vbase : i + 1;
+            const int2 ri = S.v[i], rj = S.v[nx];
+            const int4 f = sm.pfr[q];
+            float4 rec;
+            if (!f.w) {
+                const int dx = rj.x - ri.x, dy = rj.y - ri.y;
+                const float fdx = __int2float_rn(dx), fdy = __int2float_rn(dy);
+                const float X = __int2float_rn(ri.x - f.x), Y = __int2float_rn(ri.y - f.y);
+                const float c = __fmaf_rn(X, fdy, -__fmul_rn(Y, fdx));
+                rec = dy > 0 ? make_float4(c, fdy, fdx, __int_as_float(rj.y))
+                             : make_float4(-c, -fdy, -fdx, __int_as_float(rj.y));
+            } else {
+                rec = wide_record(ri, rj, f.x, f.y);
+            }
+            sm.rec[i] = rec;
+        }
+        // ---- queue the candidates inside their polygon's box: short polygons from the front,
+        //      longer ones from the back, so that a warp's lanes walk similar edge counts
+        for (int i0 = 0; i0 < nc; i0 += PM_CONS) {
+            const int i = i0 + tid;
+            bool in = false, shrt = false;
+            if (i < nc) {
+                const int q = sm.cp[i];
+                if (q != 0xffff) {
+                    const int2 p = S.pts[i];
+                    const int4 b = sm.pbox[q];
+                    in = p.x >= b.x && p.x <= b.z && p.y >= b.y && p.y <= b.w;
+                    shrt = S.po[q + 1] - S.po[q] <= PM_SHORT;
+                    ++st_cand;
+                }
+            }
+            const unsigned ms = __ballot_sync(FULL, in && shrt), ml = __ballot_sync(FULL, in && !shrt);
+            int fb = 0, bb = 0;
+            if (lane == 0) {
+                if (ms) fb = atomicAdd(&sm.qfront, __popc(ms));
+                if (ml) bb = atomicSub(&sm.qback, __popc(ml)) - __popc(ml);
+            }
+            fb = __shfl_sync(FULL, fb, 0);
+            bb = __shfl_sync(FULL, bb, 0);
+            const unsigned below = (1u << lane) - 1u;
+            if (in && shrt) sm.queue[fb + __popc(ms & below)] = (unsigned short)i;
+            if (in && !shrt) sm.queue[bb + __popc(ml & below)] = (unsigned short)i;
+        }
+        bar_sync(BAR_CONS, PM_CONS);
+        const int nf = sm.qfront, nb = sm.qback;
+        const int nq = nf + (PM_TC - nb);
+        if (tid == 0) st_rej -= (unsigned)nq;
+        // ---- the edge loop, one queued candidate per thread
+        const int sh = (int)(cb0 & 31);   // bit of candidate cb0 within its word
+        for (int t = tid; t < nq; t += PM_CONS) {
+            const int i = sm.queue[t < nf ? t : nb + (t - nf)];
+            const int q = sm.cp[i];
+            const int2 p = S.pts[i];
+            const int4 f = sm.pfr[q];
+            const int e0 = S.po[q] - vbase, e1 = S.po[q + 1] - vbase;
+            const float B = __int_as_float(f.z);
+            const float Px = __int2float_rn(p.x - f.x), Py = __int2float_rn(p.y - f.y);
+            bool sp = S.v[e0].y > p.y;
+            int parity = 0;
+            bool unc = false;
+            #pragma unroll 2
+            for (int e = e0; e < e1; ++e) {
+                const float4 q4 = sm.rec[e];
+                const bool sn = __float_as_int(q4.w) > p.y;
+                const bool st = sn != sp;
+                sp = sn;
+                float tt = __fmaf_rn(-Px, q4.y, q4.x);
+                tt = __fmaf_rn(Py, q4.z, tt);
+                parity ^= (int)(st & (tt > 0.f));
+                unc |= st & (fabsf(tt) <= B);
+            }
+            if (unc) {
+                ++st_fbp;
+                parity = exact_parity(S.v, e0, e1, true, p);
+            }
+            if (parity) {
+                const int b = sh + i;
+                atomicOr(&sm.words[b >> 5], 1u << (b & 31));
+            }
+        }
+        // the stage's data is no longer needed
+        __threadfence_block();
+        bar_arrive(BAR_EMPTY + (j & 1), PM_THREADS);
+        bar_sync(BAR_CONS, PM_CONS);
+        // ---- write the pass's words: bits [sh, sh + nc) of words cb0 >> 5 ...
+        const int nwd = (sh + nc + 31) >> 5;
+        for (int t = tid; t < nwd; t += PM_CONS)
+            masked_store(a.out_bits + (cb0 >> 5) + t, range_mask(t == 0 ? sh : 0, min(32, sh + nc - 32 * t)),
+                         sm.words[t]);
     }
     if (a.stats) {
         st_rej += st_cand;
@@ -656,26 +735,27 @@ static int ensure_smem(K kernel, size_t smem, size_t *configured)
 }
 
 template <bool DENSE>
-static int launch_poly_d(const ClassifyArgs &a, long long total_bits, LargeList *ll, int lcap, int n_sm,
+static int launch_pipe_d(const ClassifyArgs &a, long long total_bits, LargeList *ll, int lcap, int n_sm,
                          cudaStream_t stream)
 {
+    using CI = typename std::conditional<DENSE, long long, int>::type;
     static size_t configured[64] = {0};
     static int blocks_per_sm[64] = {0};
-    const size_t smem = sizeof(PolySmem);
-    int e = ensure_smem(k_pip_poly<DENSE>, smem, configured);
+    const size_t smem = sizeof(PipeSmem<CI>);
+    int e = ensure_smem(k_pip_pipe<DENSE>, smem, configured);
     if (e) return e;
     int dev = 0;
     cudaGetDevice(&dev);
     if (dev >= 0 && dev < 64 && blocks_per_sm[dev] == 0) {
         int nb = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_pip_poly<DENSE>, PM_THREADS, smem) != cudaSuccess)
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_pip_pipe<DENSE>, PM_THREADS, smem) != cudaSuccess)
             nb = 1;
         blocks_per_sm[dev] = std::max(nb, 1);
     }
     const int bps = (dev >= 0 && dev < 64) ? blocks_per_sm[dev] : 1;
     const long long nchunk = ((long long)a.n_polys + PM_NP - 1) / PM_NP;
     const int grid = (int)std::max(1LL, std::min((long long)n_sm * bps, nchunk));
-    k_pip_poly<DENSE><<<grid, PM_THREADS, smem, stream>>>(a, total_bits, ll, lcap);
+    k_pip_pipe<DENSE><<<grid, PM_THREADS, smem, stream>>>(a, total_bits, ll, lcap);
     return (int)cudaGetLastError();
 }
 
@@ -695,8 +775,8 @@ static int launch_large_ppt(const ClassifyArgs &a, long long total_bits, LargeLi
 int launch_filtered(const ClassifyArgs &a, long long total_bits, const Tuning &t, int n_sm, LargeList *ll, int lcap,
                     cudaStream_t stream)
 {
-    int e = a.cand_offsets ? launch_poly_d<false>(a, total_bits, ll, lcap, n_sm, stream)
-                           : launch_poly_d<true>(a, total_bits, ll, lcap, n_sm, stream);
+    int e = a.cand_offsets ? launch_pipe_d<false>(a, total_bits, ll, lcap, n_sm, stream)
+                           : launch_pipe_d<true>(a, total_bits, ll, lcap, n_sm, stream);
     if (e) return e;
     const int grid = n_sm * t.ctas_per_sm;
     switch (t.pts_per_thread) {
