@@ -109,22 +109,81 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def oracle_baseline(w, target_s=10.0, max_reps=20):
-    """The CPU oracle on the whole batch, repeated until ~target_s of CPU work."""
+def oracle_baseline(w, target_s=10.0, max_reps=20, max_pairs=2e10):
+    """The CPU oracle on the whole batch, repeated until ~target_s of CPU work; for batches
+    above max_pairs pair tests, on a seeded sample of candidates instead."""
+    import numpy as np
     import oracle
     threads = oracle.default_threads()
     oracle.build()
-    reps, t_total = 0, 0.0
-    while reps < max_reps and (t_total < target_s or reps == 0):
-        t0 = time.perf_counter()
-        oracle.classify(w.points, w.poly_offsets, w.verts, w.cand_offsets, w.cand_ids, threads=threads)
-        t_total += time.perf_counter() - t0
-        reps += 1
     T = w.pair_tests()
-    return {"value": T * reps / t_total, "unit": UNIT, "cores": threads, "kind": "oracle",
-            "sample": f"whole {w.name} batch ({w.n_polys} polygons, {w.n_candidates} candidates, "
-                      f"{T} pair tests) x {reps} runs, {t_total:.1f} s",
-            "points_per_s": w.n_candidates * reps / t_total}
+    if T <= max_pairs:
+        reps, t_total = 0, 0.0
+        while reps < max_reps and (t_total < target_s or reps == 0):
+            t0 = time.perf_counter()
+            oracle.classify(w.points, w.poly_offsets, w.verts, w.cand_offsets, w.cand_ids, threads=threads)
+            t_total += time.perf_counter() - t0
+            reps += 1
+        return {"value": T * reps / t_total, "unit": UNIT, "cores": threads, "kind": "oracle",
+                "sample": f"whole {w.name} batch ({w.n_polys} polygons, {w.n_candidates} candidates, "
+                          f"{T} pair tests) x {reps} runs, {t_total:.1f} s",
+                "points_per_s": w.n_candidates * reps / t_total}
+    # sampled: candidates drawn uniformly, classified one by one (threaded over the sample)
+    rng = np.random.default_rng(12345)
+    m = np.diff(w.poly_offsets.astype(np.int64))
+    owner = np.repeat(np.arange(w.n_polys), np.diff(w.cand_offsets.astype(np.int64)))
+    n = max(64, int(len(owner) * max_pairs / 20 / T))
+    sample = np.sort(rng.choice(len(owner), size=min(n, len(owner)), replace=False))
+    pairs = int(m[owner[sample]].sum())
+    t0 = time.perf_counter()
+    _threaded_sample(w, sample, threads)
+    dt = time.perf_counter() - t0
+    return {"value": pairs / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"{len(sample)} seeded candidates of the {w.name} batch ({pairs} pair tests), {dt:.1f} s",
+            "points_per_s": len(sample) / dt}
+
+
+def _threaded_sample(w, sample, threads):
+    import numpy as np
+    import oracle
+    from concurrent.futures import ThreadPoolExecutor
+    parts = np.array_split(sample, threads)
+    with ThreadPoolExecutor(threads) as ex:
+        list(ex.map(lambda s_: oracle.classify_sample(w.points, w.poly_offsets, w.verts, s_, w.cand_offsets,
+                                                      w.cand_ids), parts))
+
+
+KERNEL_SOURCES = ["paper_2306_04316_gb300/csrc/pip_filtered.cu", "paper_2306_04316_gb300/csrc/pip_device.cuh",
+                  "paper_2306_04316_gb300/csrc/pip_launch.h"]
+
+
+def kernel_source_hash():
+    import hashlib
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(workload):
+    """DRAM bytes per launch of the classify kernel from the committed ncu summary, or None when
+    the kernel sources changed since that capture (or no summary covers this workload)."""
+    path = os.path.join(ROOT, "profiles", f"k_pip_pipe_{workload}.md")
+    if not os.path.exists(path):
+        return None
+    vals = {}
+    with open(path) as fh:
+        for line in fh:
+            if line.startswith("- ") and ": " in line:
+                k, v = line[2:].split(": ", 1)
+                vals[k.strip()] = v.strip().strip("`")
+    if vals.get("kernel source sha256[:16]") != kernel_source_hash():
+        return None
+    try:
+        return int(vals["dram bytes per launch (read + write)"])
+    except (KeyError, ValueError):
+        return None
 
 
 def make_workload(name, rank, scale):
@@ -135,6 +194,8 @@ def make_workload(name, rank, scale):
         return W.stress(seed=W.BASE_SEED + 5 + 1000 * rank, n_polys=int(1_000_000 * scale))
     if name == "star":
         return W.star(seed=W.BASE_SEED + 1 + 1000 * rank)
+    if name == "fractal":
+        return W.fractal(seed=W.BASE_SEED + 4 + 1000 * rank, n_points=int(10_000_000 * scale))
     raise SystemExit(f"unknown workload {name}")
 
 
@@ -176,18 +237,114 @@ def run_reference(args, rank, world):
     return 0
 
 
+def run_join(args, rank, world):
+    """Spatial join: 100k footprint polygons against 20 batches of 10M clustered points; one
+    step = one replay of a CUDA graph that bins and classifies all 20 batches."""
+    import numpy as np
+    import torch
+    from paper_2306_04316_gb300 import api, build as pbuild, workloads as W
+
+    pbuild.build_library()
+    torch.cuda.set_device(_env_int("LOCAL_RANK", 0))
+    nb = args.batches
+    n_pts = int(10_000_000 * args.scale)
+    seed = W.BASE_SEED + 3 + 1000 * rank
+    clusters, po, v = W.join_polygons(seed=seed, n_polys=int(100_000 * max(args.scale, 0.01)))
+    P = len(po) - 1
+    d_po, d_v = torch.from_numpy(po).cuda(), torch.from_numpy(v).cuda()
+    host_pts = [W.join_points(clusters, seed + 1000 + b, n_pts) for b in range(nb)]
+    d_pts = [torch.from_numpy(x).cuda() for x in host_pts]
+    stream = torch.cuda.Stream()
+    ws = api.bin_workspace(n_pts, P)
+    co = [torch.empty(P + 1, dtype=torch.int32, device="cuda") for _ in range(nb)]
+    tot = [torch.empty(1, dtype=torch.int64, device="cuda") for _ in range(nb)]
+    with torch.cuda.stream(stream):
+        totals = []
+        for b in range(nb):
+            api.pip_bin_count(d_pts[b], d_po, d_v, workspace=ws, cand_offsets=co[b], d_total=tot[b], stream=stream)
+            stream.synchronize()
+            totals.append(int(tot[b].item()))
+    cap = int(max(totals) * 1.1) + 1024
+    ids = [torch.empty(cap, dtype=torch.int32, device="cuda") for _ in range(nb)]
+    outs = [torch.empty(cap // 32 + 1, dtype=torch.int32, device="cuda") for _ in range(nb)]
+    ovf = torch.zeros(nb, dtype=torch.int32, device="cuda")
+
+    def one_pass(classify=True):
+        for b in range(nb):
+            api.pip_bin_count(d_pts[b], d_po, d_v, workspace=ws, cand_offsets=co[b], d_total=tot[b], stream=stream)
+            api.pip_bin_fill(d_pts[b], d_po, d_v, ws, co[b], ids[b], d_overflow=ovf[b:b + 1], stream=stream)
+            if classify:
+                api.pip_classify(d_pts[b], d_po, d_v, co[b], ids[b], out=outs[b], stream=stream)
+
+    with torch.cuda.stream(stream):
+        one_pass()
+        one_pass()
+    stream.synchronize()
+    assert int(ovf.sum().item()) == 0
+    m = np.diff(po.astype(np.int64))
+    T = sum(int((m * np.diff(c.cpu().numpy().astype(np.int64))).sum()) for c in co)
+    C = sum(int(c[-1].item()) for c in co)
+    graphs = {}
+    for name, cls in (("full", True), ("binning", False)):
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=stream):
+            one_pass(cls)
+        graphs[name] = g
+    res = {}
+    for name, g in graphs.items():
+        with torch.cuda.stream(stream):
+            for _ in range(args.warmup):
+                g.replay()
+        stream.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        sampler = ClockSampler(_env_int("LOCAL_RANK", 0)) if name == "full" else None
+        if sampler:
+            sampler.start()
+        e0.record(stream)
+        with torch.cuda.stream(stream):
+            for _ in range(args.steps):
+                g.replay()
+        e1.record(stream)
+        stream.synchronize()
+        res[name] = (e0.elapsed_time(e1) / args.steps, sampler.stop() if sampler else None)
+    ms, clocks = res["full"]
+    bin_ms = res["binning"][0]
+    bin_bytes = nb * (n_pts * 8 * 3 + n_pts * 4 * 2 * 2 * 3 + P * 16)   # rough: reads/writes of the passes
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        sub_p = min(P, 2000)
+        sub = W.Workload("join-sample", host_pts[0][:1_000_000], po[:sub_p + 1], v[:int(po[sub_p])])
+        co_s, ids_s = W.bbox_csr(sub.poly_offsets.astype(np.int64), sub.verts, sub.points)
+        cpu = oracle_baseline(sub.with_csr(co_s, ids_s, name="join-sample"))
+        cpu["sample"] = f"first {sub_p} polygons x first 1M points of batch 0 (numpy closed-bbox CSR): " + cpu["sample"]
+    if rank == 0:
+        line = {"metric": METRIC, "value": T / (ms / 1000.0), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32+i64", "data": "synthetic",
+                "config": {"workload": f"join: {P} polygons x {nb} batches of {n_pts} clustered points, "
+                                       f"{C} candidates from GPU binning, one CUDA-graph replay per step",
+                           "pair_tests_per_step": T, "candidates_per_step": C, "binning_ms_per_step": bin_ms,
+                           "classify_ms_per_step": ms - bin_ms, "l2": "inputs larger than L2 (no flush)"},
+                "points_per_s": nb * n_pts / (ms / 1000.0), "cpu_baseline": cpu, "clocks": clocks,
+                "gpu_launches": None, "roofline": None, "e2e": None}
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="footprints", choices=["footprints", "stress", "star"])
+    ap.add_argument("--workload", default="footprints", choices=["footprints", "stress", "star", "fractal", "join"])
     ap.add_argument("--kernel", default="filtered", choices=["filtered", "exact"])
     ap.add_argument("--scale", type=float, default=1.0, help="fraction of the full batch (tests only)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=20)
+    ap.add_argument("--batches", type=int, default=20, help="join workload: point batches per step")
+    ap.add_argument("--tuning", default="", help="edge_tile,pts_per_warp,ctas_per_sm,pts_per_thread (0 = keep)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -196,6 +353,8 @@ def main():
     local = _env_int("LOCAL_RANK", 0)
     if args.impl == "reference":
         return run_reference(args, rank, world)
+    if args.workload == "join":
+        return run_join(args, rank, world)
 
     import numpy as np
     import torch
@@ -203,6 +362,8 @@ def main():
 
     pbuild.build_library()
     torch.cuda.set_device(local)
+    if args.tuning:
+        api.pip_set_tuning(*[int(x) for x in args.tuning.split(",")])
     dist = None
     if world > 1:
         import torch.distributed as dist
@@ -310,16 +471,17 @@ def main():
     bound = "hbm" if t_hbm >= t_alu else "alu"
     achieved_gbs = B / (kern_ms / 1000.0) / 1e9
     achieved_pairs = T / (kern_ms / 1000.0)
+    traffic = profiled_traffic(args.workload) if args.kernel == "filtered" and args.scale == 1.0 else None
     if bound == "hbm":
         roof = {"bound": "hbm", "achieved": achieved_gbs, "peak": float(peaks["hbm_gbs"]), "unit": "GB/s",
-                "frac": achieved_gbs / float(peaks["hbm_gbs"]), "traffic": None,
-                "peak_source": peak_kind, "kernel": "k_pip_filtered" if args.kernel == "filtered" else "k_pip_exact",
+                "frac": achieved_gbs / float(peaks["hbm_gbs"]), "traffic": traffic,
+                "peak_source": peak_kind, "kernel": "k_pip_pipe + k_pip_large" if args.kernel == "filtered" else "k_pip_exact",
                 "algorithmic_bytes": B, "kernel_ms": kern_ms}
     else:
         roof = {"bound": "alu", "achieved": achieved_pairs / 1e12, "peak": pair_peak / 1e12,
-                "unit": "Tpair/s", "frac": achieved_pairs / pair_peak, "traffic": None,
+                "unit": "Tpair/s", "frac": achieved_pairs / pair_peak, "traffic": traffic,
                 "peak_source": f"{n_sm} SMs x 128 lanes x {f_max / 1e6:.0f} MHz / 4 lane-instructions per pair",
-                "kernel": "k_pip_filtered" if args.kernel == "filtered" else "k_pip_exact",
+                "kernel": "k_pip_pipe + k_pip_large" if args.kernel == "filtered" else "k_pip_exact",
                 "algorithmic_bytes": B, "kernel_ms": kern_ms}
 
     cpu = None
@@ -341,7 +503,7 @@ def main():
             "roofline": roof,
             "cpu_baseline": cpu,
             "e2e": e2e,
-            "gpu_launches": args.steps,
+            "gpu_launches": args.steps * (2 if args.kernel == "filtered" else 1),
             "clocks": clocks,
             "other_kernel": {"kernel": "exact" if args.kernel == "filtered" else "filtered",
                              "ms_per_step": other_ms,

@@ -70,7 +70,6 @@ typedef struct pip_stats {
     uint64_t bbox_rejects;     /* candidates outside their polygon's bounding box */
     uint64_t fallback_points;  /* candidates re-tested exactly because an FP32 sign was
                                   within the forward-error bound of zero */
-    uint64_t fallback_edges;   /* edges whose FP32 sign was within the bound (re-tested) */
     uint64_t exact_candidates; /* candidates classified by pip_classify_exact */
 } pip_stats;
 

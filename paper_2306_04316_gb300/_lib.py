@@ -28,7 +28,6 @@ class PipStats(ctypes.Structure):
     _fields_ = [("candidates", ctypes.c_uint64),
                 ("bbox_rejects", ctypes.c_uint64),
                 ("fallback_points", ctypes.c_uint64),
-                ("fallback_edges", ctypes.c_uint64),
                 ("exact_candidates", ctypes.c_uint64)]
 
 

@@ -27,7 +27,7 @@ std::mutex g_mu;
 DeviceState g_dev[MAX_DEVICES];
 std::atomic<int> g_edge_tile{2048};
 std::atomic<int> g_ppw{128};
-std::atomic<int> g_ctas{2};
+std::atomic<int> g_ctas{4};
 std::atomic<int> g_ppt{2};
 thread_local int g_last_cuda = 0;
 
@@ -220,7 +220,6 @@ int pip_get_stats(pip_stats *out)
     out->candidates = h[ST_CANDIDATES];
     out->bbox_rejects = h[ST_BBOX_REJECTS];
     out->fallback_points = h[ST_FALLBACK_POINTS];
-    out->fallback_edges = h[ST_FALLBACK_EDGES];
     out->exact_candidates = h[ST_EXACT_CANDIDATES];
     return PIP_OK;
 }

@@ -22,7 +22,6 @@ enum StatIdx {
     ST_CANDIDATES = 0,
     ST_BBOX_REJECTS = 1,
     ST_FALLBACK_POINTS = 2,
-    ST_FALLBACK_EDGES = 3,
     ST_EXACT_CANDIDATES = 4,
     ST_COUNT = 8
 };

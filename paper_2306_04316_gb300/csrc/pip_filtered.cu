@@ -13,20 +13,17 @@
 //     c' = s (X_i d_y - Y_i d_x)   (X = x - o_x, Y = y - o_y, s = sign(d_y))
 //     a = |d_y|,  b = s d_x
 // and per (point, edge) pair the kernel evaluates t = fma(P_y, b, fma(-P_x, a, c')) with
-// P = p - o rounded to FP32, so that t approximates s * det.
-//   * k_pip_large forms c' exactly (int64, or double when M >= 2^30) and rounds it once.
-//     With S = M_x |d_y| + M_y |d_x| and u = 2^-24, rounding c' costs <= (u + 2^-51) S,
-//     rounding P_x, P_y, a, b costs <= (2u + u^2) S in the two products, and the two fused
-//     operations cost <= u (2 + 4u) S and <= u (3 + 8u) S: in total < 8.01 u S, dominated by
-//     the per-edge bound B_e = 8.5 u S.
-//   * k_pip_poly forms the record in FP32 (see PM_BOUND_K): the error is below
-//     12u (M_x H + M_y W) with H, W the polygon's height and width, dominated by the
-//     polygon-wide bound B = 13 u (M_x H + M_y W).
-// Every bound is evaluated with upward rounding.  |t| > B implies sign(t) = sign(s det) and
-// det != 0; only a straddling pair with |t| <= B needs the exact 64/128-bit recheck, which
-// runs in place.  A point outside its polygon's closed bounding box is outside the polygon
-// (the number of straddling edges is even and every crossing lies on one side of p), so it
-// skips the edge loop.
+// P = p - o rounded to FP32, so that t approximates s * det.  The record is formed in FP32
+// from the exact integer differences (int64 and double when the box is 2^30 or more wide):
+// rounding the four record inputs, the product Y d_x and the fused X d_y - Y d_x, then P_x,
+// P_y and the two per-pair fused operations, costs at most 5u|X d_y| + 6u|Y d_x| +
+// 4u|P_x d_y| + 3u|P_y d_x| (+ O(u^2)) <= 12u (M_x H + M_y W), u = 2^-24, H and W the box's
+// height and width (>= |d_y|, |d_x| of every edge in it).  The bound B = 13u (M_x H + M_y W),
+// evaluated with upward rounding, dominates it: |t| > B implies sign(t) = sign(s det) and
+// det != 0, and only a straddling pair with |t| <= B needs the exact 64/128-bit recheck,
+// which runs in place.  A point outside its polygon's closed bounding box is outside the
+// polygon (the number of straddling edges is even and every crossing lies on one side of
+// p), so it skips the edge loop.
 //
 // Two kernels, launched back to back on the caller's stream:
 //
@@ -61,31 +58,9 @@
 
 namespace pipdev {
 
-constexpr float FT_BOUND_K = 5.066394805908203125e-07f;  // 8.5 * 2^-24 (exact in FP32)
 
 // large-polygon kernel geometry
 constexpr int LG_THREADS = 256;
-
-struct Frame {
-    int ox, oy;
-    float mx, my;   // upper bounds of |x - ox|, |y - oy| over the frame's box
-    int wide;       // M >= 2^30: form c' in double
-};
-
-__device__ __forceinline__ Frame make_frame(int xmin, int ymin, int xmax, int ymax)
-{
-    Frame f;
-    const long long ox = (long long)xmin + (((long long)xmax - xmin) >> 1);
-    const long long oy = (long long)ymin + (((long long)ymax - ymin) >> 1);
-    const long long Mx = max((long long)xmax - ox, ox - xmin);
-    const long long My = max((long long)ymax - oy, oy - ymin);
-    f.ox = (int)ox;
-    f.oy = (int)oy;
-    f.mx = __ll2float_ru(Mx);
-    f.my = __ll2float_ru(My);
-    f.wide = (Mx >= (1LL << 30)) | (My >= (1LL << 30));
-    return f;
-}
 
 // c' = s (X_i d_y - Y_i d_x) rounded to FP32 (s = sign(d_y)).
 __device__ __forceinline__ float edge_c(int2 ri, long long dx, long long dy, int ox, int oy, int wide)
@@ -100,20 +75,7 @@ __device__ __forceinline__ float edge_c(int2 ri, long long dx, long long dy, int
     return dy > 0 ? c : -c;
 }
 
-__device__ __forceinline__ float bound_of(float mx, float my, long long adx, long long ady)
-{
-    return __fmul_ru(FT_BOUND_K, __fadd_ru(__fmul_ru(mx, __ll2float_ru(ady)), __fmul_ru(my, __ll2float_ru(adx))));
-}
 
-// Large-kernel edge record: (c', |d_y|, s d_x, B_e).  Horizontal edges never straddle.
-__device__ __forceinline__ float4 make_record(int2 ri, int2 rj, const Frame &f)
-{
-    const long long dx = (long long)rj.x - ri.x, dy = (long long)rj.y - ri.y;
-    if (dy == 0) return make_float4(0.f, 0.f, 0.f, 0.f);
-    const long long ady = dy > 0 ? dy : -dy, adx = dx >= 0 ? dx : -dx;
-    return make_float4(edge_c(ri, dx, dy, f.ox, f.oy, f.wide), __ll2float_rn(ady),
-                       __ll2float_rn(dy > 0 ? dx : -dx), bound_of(f.mx, f.my, adx, ady));
-}
 
 // Edge record of a frame 2^30 or more wide (int64 and double arithmetic; rare, out of line).
 __device__ __noinline__ float4 wide_record(int2 ri, int2 rj, int ox, int oy)
@@ -462,7 +424,7 @@ __global__ void __launch_bounds__(PM_THREADS, 3) k_pip_pipe(ClassifyArgs a, long
             const int4 f = sm.pfr[q];
             const int e0 = S.po[q] - vbase, e1 = S.po[q + 1] - vbase;
             const float B = __int_as_float(f.z);
-            const float Px = __int2float_rn(p.x - f.x), Py = __int2float_rn(p.y - f.y);
+            const float Px = __ll2float_rn((long long)p.x - f.x), Py = __ll2float_rn((long long)p.y - f.y);
             bool sp = S.v[e0].y > p.y;
             int parity = 0;
             bool unc = false;
@@ -523,50 +485,72 @@ size_t filtered_smem_bytes(int T)
     return (b + 15) & ~(size_t)15;
 }
 
-// Parity over the tile's edges 0..nt-1 (edge e from s_v[e] to s_v[e + 1]).
-__device__ __forceinline__ int tile_parity(const float4 *__restrict__ s_rec, const int2 *__restrict__ s_v, int nt,
-                                           int2 p, const Frame &f, unsigned long long &n_fb_pts,
-                                           unsigned long long &n_fb_edges)
+// Parities of a thread's PPT candidates over the tile's edges 0..nt-1 (edge e from s_v[e] to
+// s_v[e + 1]; record e holds the edge's bound in .w): one shared record load serves every
+// candidate, and the PPT chains are independent.  Candidates whose FP32 sign came within the
+// bound of zero are redone exactly.
+template <int PPT>
+__device__ __forceinline__ void tile_parity_multi(const float4 *__restrict__ s_rec, const int2 *__restrict__ s_v,
+                                                  int nt, const int2 (&p)[PPT], const bool (&ok)[PPT], int ox,
+                                                  int oy, int (&par)[PPT], unsigned long long &n_fb_pts)
 {
-    const float Px = __ll2float_rn((long long)p.x - f.ox);
-    const float Py = __ll2float_rn((long long)p.y - f.oy);
-    bool sp = s_v[0].y > p.y;
-    int parity = 0, unc = 0;
-    for (int e = 0; e < nt; ++e) {
-        const float4 q = s_rec[e];
-        const bool s = s_v[e + 1].y > p.y;
-        const bool st = s != sp;
-        sp = s;
-        float t = __fmaf_rn(-Px, q.y, q.x);
-        t = __fmaf_rn(Py, q.z, t);
-        parity ^= (int)(st & (t > 0.f));
-        unc += (int)(st & (fabsf(t) <= q.w));
+    // one candidate at a time: the side of the previous vertex is carried in one predicate
+    #pragma unroll 1
+    for (int r = 0; r < PPT; ++r) {
+        if (!ok[r]) continue;
+        const float Px = __ll2float_rn((long long)p[r].x - ox);
+        const float Py = __ll2float_rn((long long)p[r].y - oy);
+        const int py = p[r].y;
+        bool sp = s_v[0].y > py;
+        int pr = 0, unc = 0;
+        #pragma unroll 2
+        for (int e = 0; e < nt; ++e) {
+            const float4 q = s_rec[e];
+            const bool sn = s_v[e + 1].y > py;
+            const bool st = sn != sp;
+            sp = sn;
+            float t = __fmaf_rn(-Px, q.y, q.x);
+            t = __fmaf_rn(Py, q.z, t);
+            pr ^= (int)(st & (t > 0.f));
+            unc += (int)(st & (fabsf(t) <= q.w));
+        }
+        if (unc) {
+            ++n_fb_pts;
+            pr = exact_parity(s_v, 0, nt, false, p[r]);
+        }
+        par[r] ^= pr;
     }
-    if (unc) {
-        ++n_fb_pts;
-        n_fb_edges += (unsigned long long)unc;
-        parity = exact_parity(s_v, 0, nt, false, p);
-    }
-    return parity;
+}
+
+// Edges per work item of a large polygon with m edges and nb candidate blocks: slices short
+// enough that the listed polygons give every CTA about two items, never below 256 edges or
+// above 16,384, a multiple of 32.  Every CTA derives the same value.
+__device__ __forceinline__ int slice_edges(long long m, long long nb, int nlarge, int grid)
+{
+    const long long want = (2LL * grid + max(nlarge, 1) - 1) / max(nlarge, 1);
+    const long long ns = max(1LL, (want + nb - 1) / max(nb, 1LL));
+    long long es = (m + ns - 1) / ns;
+    es = min(16384LL, max(256LL, es));
+    return (int)((es + 31) & ~31LL);
 }
 
 template <int PPT>
 __global__ void __launch_bounds__(LG_THREADS) k_pip_large(ClassifyArgs a, long long total_bits, LargeList *ll,
-                                                         int lcap, int T, int ES)
+                                                         int lcap, int T)
 {
     extern __shared__ __align__(16) unsigned char dsm[];
     float4 *s_rec = reinterpret_cast<float4 *>(dsm);
     int2 *s_v = reinterpret_cast<int2 *>(s_rec + T);
     __shared__ int s_item[4];          // polygon, candidate block, edge slice, valid
     __shared__ int s_pb[4], s_tb[4];
-    __shared__ Frame s_tf;
+    __shared__ int s_tf[4];            // tile frame: ox, oy, bound (float bits), wide
 
     constexpr int CB = LG_THREADS * PPT;
     const int tid = threadIdx.x, lane = tid & 31;
     const bool dense = a.cand_offsets == nullptr;
     const int P = a.n_polys;
     const long long W32 = a.words_per_poly * 32;
-    unsigned long long st_cand = 0, st_fbp = 0, st_fbe = 0;
+    unsigned long long st_cand = 0, st_fbp = 0;
     const int count = *((volatile int *)&ll->count);
     const bool scan = *((volatile int *)&ll->overflow) != 0;
     long long scan_k = blockIdx.x;   // overflow mode: polygons blockIdx.x, + gridDim.x, ...
@@ -583,10 +567,12 @@ __global__ void __launch_bounds__(LG_THREADS) k_pip_large(ClassifyArgs a, long l
                     const long long cs = dense ? k * W32 : (long long)a.cand_offsets[k];
                     const long long ce = dense ? cs + W32 : (long long)a.cand_offsets[k + 1];
                     const long long m = (long long)a.poly_offsets[k + 1] - a.poly_offsets[k];
-                    const long long nb = (ce - cs + CB - 1) / CB, ns = (m + ES - 1) / ES;
+                    const long long nb = (ce - cs + CB - 1) / CB;
+                    const int ES = slice_edges(m, nb, count, gridDim.x);
+                    const long long ns = (m + ES - 1) / ES;
                     const int it = atomicAdd(large_taken(ll, lcap) + e, 1);
                     if ((long long)it < nb * ns) {
-                        s_item[0] = k; s_item[1] = (int)(it / ns); s_item[2] = (int)(it % ns); s_item[3] = 1;
+                        s_item[0] = k; s_item[1] = (int)(it / ns); s_item[2] = (int)(it % ns); s_item[3] = ES;
                         break;
                     }
                     atomicCAS(&ll->cursor, e, e + 1);
@@ -598,10 +584,12 @@ __global__ void __launch_bounds__(LG_THREADS) k_pip_large(ClassifyArgs a, long l
                     const long long ce = dense ? cs + W32 : (long long)a.cand_offsets[k + 1];
                     const long long m = (long long)a.poly_offsets[k + 1] - a.poly_offsets[k];
                     const long long n = dense ? min((long long)a.n_points, W32) : ce - cs;
-                    const long long nb = pm_is_large(m, n) ? (ce - cs + CB - 1) / CB : 0, ns = (m + ES - 1) / ES;
+                    const long long nb = pm_is_large(m, n) ? (ce - cs + CB - 1) / CB : 0;
+                    const int ES = slice_edges(m, nb, count, gridDim.x);
+                    const long long ns = (m + ES - 1) / ES;
                     if (scan_item < nb * ns) {
                         s_item[0] = k; s_item[1] = (int)(scan_item / ns); s_item[2] = (int)(scan_item % ns);
-                        s_item[3] = 1;
+                        s_item[3] = ES;
                         ++scan_item;
                         break;
                     }
@@ -618,6 +606,7 @@ __global__ void __launch_bounds__(LG_THREADS) k_pip_large(ClassifyArgs a, long l
         const long long cb0 = cs + (long long)s_item[1] * CB, cb1 = min(cb0 + CB, ce);
         const int base = a.poly_offsets[k];
         const int m = a.poly_offsets[k + 1] - base;
+        const int ES = s_item[3];
         const int ea = s_item[2] * ES, eb = min(m, ea + ES);
         int2 pt[PPT];
         bool ok[PPT];
@@ -665,14 +654,39 @@ __global__ void __launch_bounds__(LG_THREADS) k_pip_large(ClassifyArgs a, long l
                 atomicMin(&s_tb[0], x0); atomicMin(&s_tb[1], y0); atomicMax(&s_tb[2], x1); atomicMax(&s_tb[3], y1);
             }
             __syncthreads();
-            if (tid == 0) s_tf = make_frame(s_tb[0], s_tb[1], s_tb[2], s_tb[3]);
+            if (tid == 0) {
+                // box of the tile's vertices and the block's points, origin at its centre
+                const unsigned W = (unsigned)s_tb[2] - (unsigned)s_tb[0], H = (unsigned)s_tb[3] - (unsigned)s_tb[1];
+                const unsigned Mx = W - (W >> 1), My = H - (H >> 1);
+                s_tf[0] = s_tb[0] + (int)(W >> 1);
+                s_tf[1] = s_tb[1] + (int)(H >> 1);
+                s_tf[2] = (int)Mx;   // as unsigned
+                s_tf[3] = (int)My;
+            }
             __syncthreads();
-            const Frame f = s_tf;
-            for (int i = tid; i < nt; i += LG_THREADS) s_rec[i] = make_record(s_v[i], s_v[i + 1], f);
+            const int ox = s_tf[0], oy = s_tf[1];
+            const unsigned Mx = (unsigned)s_tf[2], My = (unsigned)s_tf[3];
+            const bool wide = (Mx >= (1u << 30)) | (My >= (1u << 30));
+            const float fMx = __uint2float_ru(Mx), fMy = __uint2float_ru(My);
+            for (int i = tid; i < nt; i += LG_THREADS) {
+                const int2 ri = s_v[i], rj = s_v[i + 1];
+                float4 rec;
+                if (!wide) {
+                    const int dx = rj.x - ri.x, dy = rj.y - ri.y;
+                    const float fdx = __int2float_rn(dx), fdy = __int2float_rn(dy);
+                    const float X = __int2float_rn(ri.x - ox), Y = __int2float_rn(ri.y - oy);
+                    const float c = __fmaf_rn(X, fdy, -__fmul_rn(Y, fdx));
+                    rec = dy > 0 ? make_float4(c, fdy, fdx, 0.f) : make_float4(-c, -fdy, -fdx, 0.f);
+                } else {
+                    rec = wide_record(ri, rj, ox, oy);
+                }
+                // the edge's own bound 13u (M_x |d_y| + M_y |d_x|) (see PM_BOUND_K)
+                const long long ady = llabs((long long)rj.y - ri.y), adx = llabs((long long)rj.x - ri.x);
+                rec.w = __fmul_ru(PM_BOUND_K, __fadd_ru(__fmul_ru(fMx, __ll2float_ru(ady)), __fmul_ru(fMy, __ll2float_ru(adx))));
+                s_rec[i] = rec;
+            }
             __syncthreads();
-            #pragma unroll
-            for (int r = 0; r < PPT; ++r)
-                if (ok[r]) par[r] ^= tile_parity(s_rec, s_v, nt, pt[r], f, st_fbp, st_fbe);
+            tile_parity_multi<PPT>(s_rec, s_v, nt, pt, ok, ox, oy, par, st_fbp);
             __syncthreads();
         }
         // XOR the partial parities into the output words (the block need not be word-aligned)
@@ -696,12 +710,10 @@ __global__ void __launch_bounds__(LG_THREADS) k_pip_large(ClassifyArgs a, long l
         for (int o = 16; o > 0; o >>= 1) {
             st_cand += __shfl_down_sync(FULL, st_cand, o);
             st_fbp += __shfl_down_sync(FULL, st_fbp, o);
-            st_fbe += __shfl_down_sync(FULL, st_fbe, o);
         }
         if (lane == 0) {
             if (st_cand) atomicAdd(a.stats + ST_CANDIDATES, st_cand);
             if (st_fbp) atomicAdd(a.stats + ST_FALLBACK_POINTS, st_fbp);
-            if (st_fbe) atomicAdd(a.stats + ST_FALLBACK_EDGES, st_fbe);
         }
     }
     // the last CTA to finish empties the list for the next call
@@ -767,8 +779,7 @@ static int launch_large_ppt(const ClassifyArgs &a, long long total_bits, LargeLi
     const size_t smem = filtered_smem_bytes(T);
     int e = ensure_smem(k_pip_large<PPT>, smem, configured);
     if (e) return e;
-    const int ES = std::max(T, (16384 / T) * T);
-    k_pip_large<PPT><<<grid, LG_THREADS, smem, stream>>>(a, total_bits, ll, lcap, T, ES);
+    k_pip_large<PPT><<<grid, LG_THREADS, smem, stream>>>(a, total_bits, ll, lcap, T);
     return (int)cudaGetLastError();
 }
 

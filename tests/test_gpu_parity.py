@@ -287,3 +287,21 @@ def test_repeated_calls_and_streams(api):
                                    n_cands=w.n_bits)
         st.synchronize()
         assert_same(out.cpu().numpy().view(np.uint32)[:w.n_words], want, w.n_bits, f"call {i}")
+
+
+def test_full_range_boxes_points_on_extremes(api):
+    """Polygons whose box spans the whole int32 range (P - o reaches 2^31) with points on the
+    extreme rows and columns, in CSR and dense mode."""
+    lo, hi = -2**31, 2**31 - 1
+    polys = [[(lo, lo), (hi, lo), (hi, hi)], [(lo, lo), (hi, hi), (lo, hi)], [(hi, lo), (hi, hi), (lo, 0)],
+             [(lo, lo), (hi, 0), (lo, hi)], [(lo, 0), (0, lo), (hi, 0), (0, hi)],
+             [(lo, lo), (hi, lo), (hi, hi), (lo, hi)]]
+    rng = np.random.default_rng(71)
+    pts = []
+    for _ in range(300):
+        t = int(rng.integers(lo, hi, endpoint=True))
+        pts += [(hi, t), (lo, t), (t, hi), (t, lo), (hi - 1, t), (lo + 1, t)]
+    pts += [(hi, hi), (lo, lo), (hi, lo), (lo, hi), (hi, 0), (0, hi), (-1, -1), (0, 0)]
+    ids = list(range(len(pts)))
+    check_full(api, make("full-range-csr", polys, pts, [ids] * len(polys)))
+    check_full(api, make("full-range-dense", polys, pts))
