@@ -344,7 +344,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--batches", type=int, default=20, help="join workload: point batches per step")
-    ap.add_argument("--tuning", default="", help="edge_tile,pts_per_warp,ctas_per_sm,pts_per_thread (0 = keep)")
+    ap.add_argument("--tuning", default="", help="edge_tile,pts_per_thread,ctas_per_sm (0 = keep)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 

@@ -133,7 +133,7 @@ int pip_classify_noalloc(const int32_t *points, int64_t n_points,
  * binning calls need for n_points points and n_polys polygons.
  *
  * pip_bin_count: bins the points (cell size `cell_size` units; 0 = chosen on the device
- * from the mean polygon extent, capped so that the grid has at most 2^22 cells), then
+ * from the mean polygon extent, capped so that the grid has at most 2^24 cells), then
  * writes cand_offsets [n_polys + 1] (device, exclusive prefix sum of the per-polygon
  * counts) and *d_total (device int64) = the number of candidates.  The grid stays in the
  * workspace for pip_bin_fill.
@@ -154,16 +154,15 @@ int pip_bin_fill(const int32_t *points, int64_t n_points,
                  int32_t *d_overflow, void *stream);
 
 /*
- * Tuning of pip_classify (the autotuner's hook; not in the paper).  0 keeps a value.
- *   edge_tile      large-polygon kernel: edges staged in shared memory per pass
- *                  (256..8192, a multiple of 32)
- *   pts_per_warp   small-polygon kernel: candidates a warp takes per group (64, 128, 256)
- *   ctas_per_sm    large-polygon kernel: resident CTAs per SM (1..8)
- *   pts_per_thread large-polygon kernel: candidates each thread carries (1, 2, 4)
+ * Tuning of pip_classify's large-polygon kernel (the autotuner's hook; not in the paper).
+ * 0 keeps a value.
+ *   edge_tile      edges staged in shared memory per pass (256..8192, a multiple of 32)
+ *   pts_per_thread candidates each thread carries through a tile (1, 2, 4)
+ *   ctas_per_sm    resident CTAs per SM of its persistent grid (1..8)
  * Applies to later calls on every device; PIP_ERR_INVALID for an out-of-range value.
  */
-int pip_set_tuning(int32_t edge_tile, int32_t pts_per_warp, int32_t ctas_per_sm, int32_t pts_per_thread);
-int pip_get_tuning(int32_t *edge_tile, int32_t *pts_per_warp, int32_t *ctas_per_sm, int32_t *pts_per_thread);
+int pip_set_tuning(int32_t edge_tile, int32_t pts_per_thread, int32_t ctas_per_sm);
+int pip_get_tuning(int32_t *edge_tile, int32_t *pts_per_thread, int32_t *ctas_per_sm);
 
 /* Statistics (device counters of the current device).  pip_get_stats copies them to the
  * host with a synchronous copy: call it after the work of interest has completed. */

@@ -55,8 +55,8 @@ _SIGS = {
     "pip_bin_workspace_bytes": ([_I64, _I32], ctypes.c_size_t),
     "pip_bin_count": ([_P, _I64, _P, _P, _I32, _I32, _P, ctypes.c_size_t, _P, _P, _P], ctypes.c_int),
     "pip_bin_fill": ([_P, _I64, _P, _P, _I32, _P, ctypes.c_size_t, _P, _P, _I64, _P, _P], ctypes.c_int),
-    "pip_set_tuning": ([_I32, _I32, _I32, _I32], ctypes.c_int),
-    "pip_get_tuning": ([_P, _P, _P, _P], ctypes.c_int),
+    "pip_set_tuning": ([_I32, _I32, _I32], ctypes.c_int),
+    "pip_get_tuning": ([_P, _P, _P], ctypes.c_int),
     "pip_get_stats": ([ctypes.POINTER(PipStats)], ctypes.c_int),
     "pip_reset_stats": ([], ctypes.c_int),
     "pip_validate": ([_P, _I64, _P, _P, _I32, _I64, _P, _P, _I64, _P, _P], ctypes.c_int),

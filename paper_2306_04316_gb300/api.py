@@ -149,13 +149,12 @@ def bin_join(points, poly_offsets, verts, cell_size=0, stream=None):
     return co, ids[:total]
 
 
-def pip_set_tuning(edge_tile=0, pts_per_warp=0, ctas_per_sm=0, pts_per_thread=0):
-    _lib.check("pip_set_tuning", _lib.load().pip_set_tuning(edge_tile, pts_per_warp, ctas_per_sm,
-                                                             pts_per_thread))
+def pip_set_tuning(edge_tile=0, pts_per_thread=0, ctas_per_sm=0):
+    _lib.check("pip_set_tuning", _lib.load().pip_set_tuning(edge_tile, pts_per_thread, ctas_per_sm))
 
 
 def pip_get_tuning():
-    v = [ctypes.c_int32() for _ in range(4)]
+    v = [ctypes.c_int32() for _ in range(3)]
     _lib.check("pip_get_tuning", _lib.load().pip_get_tuning(*[ctypes.byref(x) for x in v]))
     return tuple(x.value for x in v)
 

@@ -7,10 +7,11 @@
 //   1. polygon bounding boxes (one warp per polygon), the points' bounding box, and the mean
 //      polygon extent;
 //   2. grid parameters (one thread): cell = requested size, or the mean polygon extent,
-//      doubled until the grid has at most 2^22 cells;
+//      doubled until the grid has at most 2^24 cells;
 //   3. cell id of every point, cell histogram, exclusive scan -> cell start offsets;
-//   4. stable LSD radix sort of (cell id, point id) in three passes of 8, 8 and 6 bits (so
-//      ids ascend within a cell), then a gather of the points into cell order;
+//   4. stable LSD radix sort of (cell id, point id) in three passes of 8 bits (so
+//      ids ascend within a cell; each pass orders a tile in shared memory first so that its
+//      writes are coalesced), then a gather of the points into cell order;
 //   5. per polygon (one warp): walk the rows of cells its box covers -- each row is one
 //      contiguous range of the sorted points -- and count (pip_bin_count) or write
 //      (pip_bin_fill) the points inside the closed box, in that order.
@@ -22,7 +23,7 @@
 
 namespace pipdev {
 
-constexpr int BIN_MAX_CELLS_LOG2 = 22;
+constexpr int BIN_MAX_CELLS_LOG2 = 24;
 constexpr long long BIN_MAX_CELLS = 1LL << BIN_MAX_CELLS_LOG2;
 constexpr int RADIX_THREADS = 256;
 constexpr int RADIX_ITEMS = 16;
@@ -281,41 +282,95 @@ __global__ void __launch_bounds__(RADIX_THREADS) k_radix_scatter(const unsigned 
                                                                 int *vout, long long N, int shift, int nblk,
                                                                 const unsigned *__restrict__ hist)
 {
-    __shared__ unsigned s_base[256];
-    __shared__ unsigned s_run[256];
+    // The tile's keys are ranked stably within their digit (tile order = input order), placed
+    // in digit order in shared memory, then written out so that consecutive threads write
+    // consecutive positions of one digit's run (coalesced), at the run's global start.
+    __shared__ unsigned s_base[256];    // global start of digit d's keys from this tile
+    __shared__ unsigned s_run[256];     // keys of digit d ranked so far (then: tile count)
+    __shared__ unsigned s_lstart[256];  // tile-local start of digit d
     __shared__ unsigned s_wc[RADIX_THREADS / 32][256];
+    __shared__ unsigned s_key[RADIX_TILE];
+    __shared__ int s_val[RADIX_TILE];
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     s_base[tid] = hist[(long long)tid * nblk + blockIdx.x];
     s_run[tid] = 0;
     #pragma unroll
     for (int q = 0; q < RADIX_THREADS / 32; ++q) s_wc[q][tid] = 0;
-    __syncthreads();
     const long long base = (long long)blockIdx.x * RADIX_TILE;
-    const unsigned lt = (1u << lane) - 1u;
+    const int nt = (int)min((long long)RADIX_TILE, N - base);
+    unsigned key[RADIX_ITEMS];
+    int val[RADIX_ITEMS];
+    unsigned packed[RADIX_ITEMS];   // digit << 16 | rank within the digit
+    #pragma unroll
     for (int r = 0; r < RADIX_ITEMS; ++r) {
-        const long long i = base + r * RADIX_THREADS + tid;
-        const bool valid = i < N;
-        unsigned key = 0;
-        int val = 0;
-        if (valid) { key = kin[i]; val = vin[i]; }
-        const unsigned d = valid ? ((key >> shift) & 255u) : 256u;
+        const int i = r * RADIX_THREADS + tid;
+        key[r] = i < nt ? kin[base + i] : 0u;
+        val[r] = i < nt ? vin[base + i] : 0;
+    }
+    __syncthreads();
+    const unsigned lt = (1u << lane) - 1u;
+    #pragma unroll
+    for (int r = 0; r < RADIX_ITEMS; ++r) {
+        const bool valid = r * RADIX_THREADS + tid < nt;
+        const unsigned d = valid ? ((key[r] >> shift) & 255u) : 256u;
         const unsigned peers = __match_any_sync(FULL, d);
         const unsigned rank = __popc(peers & lt);
         if (valid && (peers & lt) == 0) s_wc[w][d] = __popc(peers);
         __syncthreads();
+        unsigned off = 0;
         if (valid) {
-            unsigned off = s_run[d] + rank;
+            off = s_run[d] + rank;
             for (int q = 0; q < w; ++q) off += s_wc[q][d];
-            const unsigned pos = s_base[d] + off;
-            kout[pos] = key;
-            vout[pos] = val;
         }
+        packed[r] = (d << 16) | off;
         __syncthreads();
         unsigned add = 0;
         #pragma unroll
         for (int q = 0; q < RADIX_THREADS / 32; ++q) { add += s_wc[q][tid]; s_wc[q][tid] = 0; }
         s_run[tid] += add;
         __syncthreads();
+    }
+    // tile-local digit starts: exclusive scan of s_run over the 256 digits
+    {
+        const unsigned c = s_run[tid];
+        unsigned incl = c;
+        #pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned t = __shfl_up_sync(FULL, incl, o);
+            if (lane >= o) incl += t;
+        }
+        if (lane == 31) s_wc[0][w] = incl;
+        __syncthreads();
+        if (w == 0) {
+            const unsigned x = lane < RADIX_THREADS / 32 ? s_wc[0][lane] : 0u;
+            unsigned xi = x;
+            #pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const unsigned t = __shfl_up_sync(FULL, xi, o);
+                if (lane >= o) xi += t;
+            }
+            if (lane < RADIX_THREADS / 32) s_wc[1][lane] = xi - x;
+        }
+        __syncthreads();
+        s_lstart[tid] = s_wc[1][w] + incl - c;
+        __syncthreads();
+    }
+    #pragma unroll
+    for (int r = 0; r < RADIX_ITEMS; ++r) {
+        if (r * RADIX_THREADS + tid < nt) {
+            const unsigned d = packed[r] >> 16;
+            const unsigned pos = s_lstart[d] + (packed[r] & 0xffffu);
+            s_key[pos] = key[r];
+            s_val[pos] = val[r];
+        }
+    }
+    __syncthreads();
+    for (int i = tid; i < nt; i += RADIX_THREADS) {
+        const unsigned k = s_key[i];
+        const unsigned d = (k >> shift) & 255u;
+        const unsigned g = s_base[d] + (unsigned)i - s_lstart[d];
+        kout[g] = k;
+        vout[g] = s_val[i];
     }
 }
 

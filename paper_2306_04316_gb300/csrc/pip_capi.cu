@@ -26,7 +26,6 @@ struct DeviceState {
 std::mutex g_mu;
 DeviceState g_dev[MAX_DEVICES];
 std::atomic<int> g_edge_tile{2048};
-std::atomic<int> g_ppw{128};
 std::atomic<int> g_ctas{4};
 std::atomic<int> g_ppt{2};
 thread_local int g_last_cuda = 0;
@@ -131,7 +130,7 @@ ClassifyArgs make_args(const int32_t *points, int64_t n_points, const int32_t *p
 }  // namespace
 
 namespace pipdev {
-Tuning current_tuning() { return Tuning{g_edge_tile.load(), g_ppw.load(), g_ctas.load(), g_ppt.load()}; }
+Tuning current_tuning() { return Tuning{g_edge_tile.load(), g_ppt.load(), g_ctas.load()}; }
 }  // namespace pipdev
 
 extern "C" {
@@ -155,7 +154,7 @@ int pip_classify(const int32_t *points, int64_t n_points, const int32_t *poly_of
     if (rc != PIP_OK) return rc;
     ClassifyArgs a = make_args(points, n_points, poly_offsets, verts, n_polys, cand_offsets, cand_ids,
                                out_bits, ds->stats);
-    Tuning t{g_edge_tile.load(), g_ppw.load(), g_ctas.load(), g_ppt.load()};
+    Tuning t = current_tuning();
     int e = launch_filtered(a, total_bits, t, ds->n_sm, ll, LARGE_LIST_CAP, s);
     return e == 0 ? PIP_OK : cuda_fail((cudaError_t)e);
 }
@@ -183,28 +182,24 @@ int pip_classify_exact(const int32_t *points, int64_t n_points, const int32_t *p
     return e == 0 ? PIP_OK : cuda_fail((cudaError_t)e);
 }
 
-int pip_set_tuning(int32_t edge_tile, int32_t pts_per_warp, int32_t ctas_per_sm, int32_t pts_per_thread)
+int pip_set_tuning(int32_t edge_tile, int32_t pts_per_thread, int32_t ctas_per_sm)
 {
     if (edge_tile != 0 && (edge_tile < 256 || edge_tile > 8192 || edge_tile % 32 != 0)) return PIP_ERR_INVALID;
-    if (pts_per_warp != 0 && pts_per_warp != 64 && pts_per_warp != 128 && pts_per_warp != 256)
-        return PIP_ERR_INVALID;
-    if (ctas_per_sm != 0 && (ctas_per_sm < 1 || ctas_per_sm > 8)) return PIP_ERR_INVALID;
     if (pts_per_thread != 0 && pts_per_thread != 1 && pts_per_thread != 2 && pts_per_thread != 4)
         return PIP_ERR_INVALID;
+    if (ctas_per_sm != 0 && (ctas_per_sm < 1 || ctas_per_sm > 8)) return PIP_ERR_INVALID;
     if (edge_tile) g_edge_tile.store(edge_tile);
-    if (pts_per_warp) g_ppw.store(pts_per_warp);
-    if (ctas_per_sm) g_ctas.store(ctas_per_sm);
     if (pts_per_thread) g_ppt.store(pts_per_thread);
+    if (ctas_per_sm) g_ctas.store(ctas_per_sm);
     return PIP_OK;
 }
 
-int pip_get_tuning(int32_t *edge_tile, int32_t *pts_per_warp, int32_t *ctas_per_sm, int32_t *pts_per_thread)
+int pip_get_tuning(int32_t *edge_tile, int32_t *pts_per_thread, int32_t *ctas_per_sm)
 {
-    if (!edge_tile || !pts_per_warp || !ctas_per_sm || !pts_per_thread) return PIP_ERR_NULL;
+    if (!edge_tile || !pts_per_thread || !ctas_per_sm) return PIP_ERR_NULL;
     *edge_tile = g_edge_tile.load();
-    *pts_per_warp = g_ppw.load();
-    *ctas_per_sm = g_ctas.load();
     *pts_per_thread = g_ppt.load();
+    *ctas_per_sm = g_ctas.load();
     return PIP_OK;
 }
 

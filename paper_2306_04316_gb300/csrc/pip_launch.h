@@ -11,12 +11,11 @@ struct ClassifyArgs;
 
 struct LargeList;
 
-// Tuned shape of pip_classify's two kernels.
+// Tuned shape of pip_classify's large-polygon kernel.
 struct Tuning {
-    int edge_tile;       // large-polygon kernel: edges staged in shared memory per pass
-    int pts_per_warp;    // batched kernel: candidates per warp group (64, 128, 256)
-    int ctas_per_sm;     // large-polygon kernel: resident CTAs per SM
-    int pts_per_thread;  // large-polygon kernel: candidates carried by each thread (1, 2, 4)
+    int edge_tile;       // edges staged in shared memory per pass
+    int pts_per_thread;  // candidates carried by each thread (1, 2, 4)
+    int ctas_per_sm;     // resident CTAs per SM
 };
 
 int launch_exact(const ClassifyArgs &a, long long total_bits, int grid, cudaStream_t stream);

@@ -81,17 +81,16 @@ def test_argument_checks_return_before_any_device_call(lib):
 
 def test_tuning_validation(lib):
     from paper_2306_04316_gb300 import _lib
-    t = [ctypes.c_int32() for _ in range(4)]
+    t = [ctypes.c_int32() for _ in range(3)]
     assert lib.pip_get_tuning(*[ctypes.byref(x) for x in t]) == 0
     before = [x.value for x in t]
-    assert lib.pip_set_tuning(100, 0, 0, 0) == _lib.PIP_ERR_INVALID      # below 256
-    assert lib.pip_set_tuning(2050, 0, 0, 0) == _lib.PIP_ERR_INVALID     # not a multiple of 32
-    assert lib.pip_set_tuning(0, 96, 0, 0) == _lib.PIP_ERR_INVALID
-    assert lib.pip_set_tuning(0, 0, 9, 0) == _lib.PIP_ERR_INVALID
-    assert lib.pip_set_tuning(0, 0, 0, 3) == _lib.PIP_ERR_INVALID
-    assert lib.pip_set_tuning(1024, 256, 2, 4) == 0
+    assert lib.pip_set_tuning(100, 0, 0) == _lib.PIP_ERR_INVALID      # below 256
+    assert lib.pip_set_tuning(2050, 0, 0) == _lib.PIP_ERR_INVALID     # not a multiple of 32
+    assert lib.pip_set_tuning(0, 3, 0) == _lib.PIP_ERR_INVALID
+    assert lib.pip_set_tuning(0, 0, 9) == _lib.PIP_ERR_INVALID
+    assert lib.pip_set_tuning(1024, 4, 2) == 0
     assert lib.pip_get_tuning(*[ctypes.byref(x) for x in t]) == 0
-    assert [x.value for x in t] == [1024, 256, 2, 4]
+    assert [x.value for x in t] == [1024, 4, 2]
     assert lib.pip_set_tuning(*before) == 0
 
 

@@ -152,8 +152,7 @@ def test_many_empty_polygons_in_one_chunk(api):
     check_full(api, make("sparse-csr", polys, pts, csr))
 
 
-@pytest.mark.parametrize("tuning", [(256, 64, 1, 1), (512, 128, 2, 2), (1024, 256, 2, 4), (2048, 128, 3, 2),
-                                    (8192, 64, 1, 1)])
+@pytest.mark.parametrize("tuning", [(256, 1, 1), (512, 2, 2), (1024, 4, 2), (2048, 2, 4), (8192, 1, 1)])
 def test_tuning_shapes(api, tuning):
     """Every tuned shape gives the same bits (small edge tiles force the streamed path)."""
     before = api.pip_get_tuning()
