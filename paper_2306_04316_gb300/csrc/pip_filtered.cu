@@ -147,7 +147,6 @@ struct __align__(16) PipeSmem {
     unsigned short cp[PM_TC];
     unsigned short queue[PM_TC];
     unsigned words[PM_TC / 32 + 2];
-    int qfront, qback;
     // producer-private
     int ids[PM_TC];
     int ppo[PM_NP + 1];
@@ -363,7 +362,6 @@ __global__ void __launch_bounds__(PM_THREADS, 3) k_pip_pipe(ClassifyArgs a, long
             for (int s = s1v; s < s1; ++s) sm.cp[s] = 0xffff;   // dense padding
         }
         for (int t = tid; t < PM_TC / 32 + 2; t += PM_CONS) sm.words[t] = 0;
-        if (tid == 0) { sm.qfront = 0; sm.qback = PM_TC; }
         bar_sync(BAR_CONS, PM_CONS);
         // ---- edge records, one thread per edge (FP32 unless the frame is 2^30 wide)
         for (int i = tid; i < nv; i += PM_CONS) {
@@ -384,68 +382,50 @@ __global__ void __launch_bounds__(PM_THREADS, 3) k_pip_pipe(ClassifyArgs a, long
             }
             sm.rec[i] = rec;
         }
-        // ---- queue the candidates inside their polygon's box: short polygons from the front,
-        //      longer ones from the back, so that a warp's lanes walk similar edge counts
-        for (int i0 = 0; i0 < nc; i0 += PM_CONS) {
+        bar_sync(BAR_CONS, PM_CONS);
+        // ---- the edge loop, candidates in order (one per thread): lanes of a warp share one or
+        //      two polygons.  A point outside its polygon's closed box is outside: its y is
+        //      replaced by INT_MAX, so no edge straddles its ray and the loop leaves 0.
+        const int sh = (int)(cb0 & 31);   // bit of candidate cb0 within its word
+        for (int i0 = 0; i0 < nc; i0 += PM_CONS) {   // warp-uniform rounds (ballot below)
             const int i = i0 + tid;
-            bool in = false, shrt = false;
-            if (i < nc) {
-                const int q = sm.cp[i];
-                if (q != 0xffff) {
-                    const int2 p = S.pts[i];
-                    const int4 b = sm.pbox[q];
-                    in = p.x >= b.x && p.x <= b.z && p.y >= b.y && p.y <= b.w;
-                    shrt = S.po[q + 1] - S.po[q] <= PM_SHORT;
-                    ++st_cand;
+            const int q = i < nc ? sm.cp[i] : 0xffff;
+            int parity = 0;
+            if (q != 0xffff) {
+                const int2 p = S.pts[i];
+                const int4 b = sm.pbox[q];
+                const bool in = p.x >= b.x && p.x <= b.z && p.y >= b.y && p.y <= b.w;
+                ++st_cand;
+                st_rej += !in;
+                const int py = in ? p.y : INT_MAX;
+                const int4 f = sm.pfr[q];
+                const int e0 = S.po[q] - vbase, e1 = S.po[q + 1] - vbase;
+                const float B = __int_as_float(f.z);
+                const float Px = __ll2float_rn((long long)p.x - f.x), Py = __ll2float_rn((long long)p.y - f.y);
+                bool sp = S.v[e0].y > py;
+                bool unc = false;
+                #pragma unroll 2
+                for (int e = e0; e < e1; ++e) {
+                    const float4 q4 = sm.rec[e];
+                    const bool sn = __float_as_int(q4.w) > py;
+                    const bool st = sn != sp;
+                    sp = sn;
+                    float tt = __fmaf_rn(-Px, q4.y, q4.x);
+                    tt = __fmaf_rn(Py, q4.z, tt);
+                    parity ^= (int)(st & (tt > 0.f));
+                    unc |= st & (fabsf(tt) <= B);
+                }
+                if (unc) {
+                    ++st_fbp;
+                    parity = exact_parity(S.v, e0, e1, true, p);
                 }
             }
-            const unsigned ms = __ballot_sync(FULL, in && shrt), ml = __ballot_sync(FULL, in && !shrt);
-            int fb = 0, bb = 0;
-            if (lane == 0) {
-                if (ms) fb = atomicAdd(&sm.qfront, __popc(ms));
-                if (ml) bb = atomicSub(&sm.qback, __popc(ml)) - __popc(ml);
-            }
-            fb = __shfl_sync(FULL, fb, 0);
-            bb = __shfl_sync(FULL, bb, 0);
-            const unsigned below = (1u << lane) - 1u;
-            if (in && shrt) sm.queue[fb + __popc(ms & below)] = (unsigned short)i;
-            if (in && !shrt) sm.queue[bb + __popc(ml & below)] = (unsigned short)i;
-        }
-        bar_sync(BAR_CONS, PM_CONS);
-        const int nf = sm.qfront, nb = sm.qback;
-        const int nq = nf + (PM_TC - nb);
-        if (tid == 0) st_rej -= (unsigned)nq;
-        // ---- the edge loop, one queued candidate per thread
-        const int sh = (int)(cb0 & 31);   // bit of candidate cb0 within its word
-        for (int t = tid; t < nq; t += PM_CONS) {
-            const int i = sm.queue[t < nf ? t : nb + (t - nf)];
-            const int q = sm.cp[i];
-            const int2 p = S.pts[i];
-            const int4 f = sm.pfr[q];
-            const int e0 = S.po[q] - vbase, e1 = S.po[q + 1] - vbase;
-            const float B = __int_as_float(f.z);
-            const float Px = __ll2float_rn((long long)p.x - f.x), Py = __ll2float_rn((long long)p.y - f.y);
-            bool sp = S.v[e0].y > p.y;
-            int parity = 0;
-            bool unc = false;
-            #pragma unroll 2
-            for (int e = e0; e < e1; ++e) {
-                const float4 q4 = sm.rec[e];
-                const bool sn = __float_as_int(q4.w) > p.y;
-                const bool st = sn != sp;
-                sp = sn;
-                float tt = __fmaf_rn(-Px, q4.y, q4.x);
-                tt = __fmaf_rn(Py, q4.z, tt);
-                parity ^= (int)(st & (tt > 0.f));
-                unc |= st & (fabsf(tt) <= B);
-            }
-            if (unc) {
-                ++st_fbp;
-                parity = exact_parity(S.v, e0, e1, true, p);
-            }
-            if (parity) {
-                const int b = sh + i;
-                atomicOr(&sm.words[b >> 5], 1u << (b & 31));
+            // pack: this warp's 32 consecutive candidates start at bit sh + i0 + 32 wid
+            const unsigned bits = __ballot_sync(FULL, parity);
+            if (lane == 0 && bits) {
+                const int bpos = sh + i0 + 32 * wid;
+                atomicOr(&sm.words[bpos >> 5], bits << (bpos & 31));
+                if (bpos & 31) atomicOr(&sm.words[(bpos >> 5) + 1], bits >> (32 - (bpos & 31)));
             }
         }
         // the stage's data is no longer needed
