@@ -169,7 +169,7 @@ def kernel_source_hash():
 def profiled_traffic(workload):
     """DRAM bytes per launch of the classify kernel from the committed ncu summary, or None when
     the kernel sources changed since that capture (or no summary covers this workload)."""
-    path = os.path.join(ROOT, "profiles", f"k_pip_pipe_{workload}.md")
+    path = os.path.join(ROOT, "profiles", f"k_pip_warp_{workload}.md")
     if not os.path.exists(path):
         return None
     vals = {}
@@ -475,13 +475,13 @@ def main():
     if bound == "hbm":
         roof = {"bound": "hbm", "achieved": achieved_gbs, "peak": float(peaks["hbm_gbs"]), "unit": "GB/s",
                 "frac": achieved_gbs / float(peaks["hbm_gbs"]), "traffic": traffic,
-                "peak_source": peak_kind, "kernel": "k_pip_pipe + k_pip_large" if args.kernel == "filtered" else "k_pip_exact",
+                "peak_source": peak_kind, "kernel": "k_pip_warp + k_pip_large" if args.kernel == "filtered" else "k_pip_exact",
                 "algorithmic_bytes": B, "kernel_ms": kern_ms}
     else:
         roof = {"bound": "alu", "achieved": achieved_pairs / 1e12, "peak": pair_peak / 1e12,
                 "unit": "Tpair/s", "frac": achieved_pairs / pair_peak, "traffic": traffic,
                 "peak_source": f"{n_sm} SMs x 128 lanes x {f_max / 1e6:.0f} MHz / 4 lane-instructions per pair",
-                "kernel": "k_pip_pipe + k_pip_large" if args.kernel == "filtered" else "k_pip_exact",
+                "kernel": "k_pip_warp + k_pip_large" if args.kernel == "filtered" else "k_pip_exact",
                 "algorithmic_bytes": B, "kernel_ms": kern_ms}
 
     cpu = None

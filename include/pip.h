@@ -74,11 +74,14 @@ typedef struct pip_stats {
 } pip_stats;
 
 /*
- * pip_classify -- the FP32-filtered batched kernels (Method, steps 2-7; Constraint 1).
- * Each polygon is rebased to a local frame; the side test (p - R_i) . n runs in FP32 with
- * a proven forward-error bound, and any (point, edge) pair whose FP32 value lies within
- * the bound is re-tested exactly with 64/128-bit integers, so the result is exact.
- * Polygons of up to 120 vertices run in a warp-per-candidate-segment kernel, larger ones in
+ * pip_classify -- the filtered batched kernels (Method, steps 2-7; Constraint 1).
+ * Each polygon is rebased to a local frame at the centre of its bounding box.  When the box
+ * is small (width, height < 2^30, width x height < 2^30) every pair test is exact in 32-bit
+ * integer arithmetic; otherwise the side test (p - R_i) . n runs in FP32 with a proven
+ * forward-error bound, and any candidate with a (point, edge) pair whose FP32 value lies
+ * within the bound is re-tested exactly with 64/128-bit integers.  The result is exact
+ * either way.  Polygons of up to 128 vertices run in a kernel where each warp takes runs of
+ * consecutive polygons; larger ones (or those with more than 2^18 candidate-edge pairs) in
  * a second kernel that splits their edges across CTAs (two launches on `stream`).  The
  * first call on a stream allocates that stream's work list and must not be captured.
  * Arguments and output layout as described above.  Returns PIP_OK or PIP_ERR_*.

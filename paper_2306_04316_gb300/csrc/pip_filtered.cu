@@ -1,4 +1,5 @@
-// FP32-filtered classification with an exact integer recheck (pip_classify).
+// Filtered classification (pip_classify): exact int32 tests for compact polygons, an FP32
+// filter with an exact integer recheck for the rest.
 //
 // Method section, steps 2-7 with Constraint 1.  For the edge R_i -> R_j of a polygon and a
 // candidate point p, the crossing counts when the straddle test (y_i > p_y) != (y_j > p_y)
@@ -25,23 +26,26 @@
 // polygon (the number of straddling edges is even and every crossing lies on one side of
 // p), so it skips the edge loop.
 //
+// Exact int32 evaluation.  When a polygon's box is small (width, height < 2^30 and width x
+// height < 2^30), det = (X_i - P_x) d_y - (Y_i - P_y) d_x of an in-box point is below 2^31 in
+// magnitude, so the same record evaluated with wrapping 32-bit integer multiply-adds gives
+// -sign(d_y) det exactly; the straddle test is the sign bit of (P_y - Y_j) XOR (P_y - Y_i).
+// No filter and no recheck are needed for such polygons (building footprints, parcels).
+//
 // Two kernels, launched back to back on the caller's stream:
 //
-// k_pip_pipe -- polygon-major, producer/consumer.  A CTA takes chunks of 128 consecutive
-//   polygons, so that every array it reads is one contiguous range: the chunk's vertex and
-//   candidate offsets, its vertices and its candidate ids; only the candidate points are
-//   gathered.  One producer warp cuts each chunk into passes (runs of whole polygons with at
-//   most 1,024 vertices and 1,024 candidates) and stages a pass's offsets, vertices and
-//   gathered points into one of two shared-memory stages with cp.async, while seven consumer
-//   warps classify the previous pass: bounding box, frame and bound per polygon, FP32 edge
-//   records per edge, then a queue of the candidates inside their polygon's box (polygons of
-//   at most 8 edges from the front, longer ones from the back, so that a warp's lanes walk
-//   similar edge counts) and the edge loop.  Named barriers hand stages back and forth.
-//   Results are packed into shared words and written out; the first and last word of a pass
-//   may be shared with a neighbouring pass, so those are written with a masked AND/OR pair
-//   that sets exactly the pass's own bits (no zero-fill pass is needed).  Polygons with more
-//   than 1,024 vertices or more than 2^18 (candidate, edge) pairs get bit 0 here and go on a
-//   device-side list.
+// k_pip_warp -- polygon-major, every warp on its own.  A warp takes chunks of 32 consecutive
+//   polygons (lane = polygon, offsets in registers) and cuts each into runs of whole polygons
+//   with at most 128 vertices and 256 candidates; a polygon with more candidates runs alone,
+//   in slices of 256.  Per run it copies the vertices and the candidate points into its own
+//   shared memory (cp.async), finds every candidate's polygon from a bitmap of polygon starts,
+//   forms each polygon's box, frame and arithmetic (lane per polygon) and the edge records
+//   (lane per edge), then classifies the candidates 32 at a time, one per lane, and packs the
+//   parities with ballots.  No barrier spans more than one warp, so the warps of an SM hide
+//   one another's memory latency.  The first and last word of a run may be shared with a
+//   neighbouring run, so those are written with a masked AND/OR pair that sets exactly the
+//   run's own bits (no zero-fill pass is needed).  Polygons with more than 128 vertices or
+//   more than 2^18 (candidate, edge) pairs get bit 0 here and go on a device-side list.
 //
 // k_pip_large -- the listed polygons.  Work items (polygon, block of 256*PPT candidates,
 //   slice of edges) are taken from the list by atomic counters; the CTA streams the slice
@@ -101,7 +105,7 @@ __device__ __noinline__ int exact_parity(const int2 *v, int e0, int e1, bool wra
 }
 
 // =============================================================================================
-// k_pip_pipe -- small polygons, polygon-major, producer/consumer
+// k_pip_warp -- small polygons; every warp works on its own runs of consecutive polygons
 // =============================================================================================
 
 // Bound factor of the FP32 records: rounding the four record inputs, the product Y d_x and the
@@ -109,55 +113,33 @@ __device__ __noinline__ int exact_parity(const int2 *v, int e0, int e1, bool wra
 // 5u|X d_y| + 6u|Y d_x| + 4u|P_x d_y| + 3u|P_y d_x| (+ O(u^2)) <= 12u (M_x H + M_y W), with H, W
 // the polygon's height and width (>= |d_y|, |d_x| of every edge).
 constexpr float PM_BOUND_K = 7.748603820800781e-07f;     // 13 * 2^-24 (exact in FP32)
-constexpr int PM_THREADS = 256;     // warps 0-6 consume, warp 7 produces
-constexpr int PM_CONS = 224;
-constexpr int PM_NP = 128;          // polygons per chunk (and at most per pass)
-constexpr int PM_TV = 1024;         // staged vertices per pass
-constexpr int PM_TC = 1024;         // staged candidates per pass
-constexpr int PM_SHORT = 8;         // polygons of at most this many edges share warps
-constexpr int PM_LARGE_M = 1024;    // polygons above this many vertices go to k_pip_large
-constexpr long long PM_LARGE_W = 1LL << 18;   // ... and those with more (candidates x vertices)
-// named barriers (0 is __syncthreads)
-constexpr int BAR_CONS = 1, BAR_FULL = 2, BAR_EMPTY = 4;
+constexpr int WP_THREADS = 256;     // 8 independent warps per CTA
+constexpr int WP_V = 128;           // vertices of a run (and most vertices of a small polygon)
+constexpr int WP_R = 8;             // candidate rounds of 32 per run
+constexpr int WP_C = 32 * WP_R;     // candidates of a run
+constexpr long long LARGE_W = 1LL << 18;   // (candidates x vertices) above which a polygon is large
+// Arithmetic of a polygon's pair tests: exact int32 when its box is small enough that every
+// value fits (width, height < 2^30 and width * height < 2^30), else the FP32 filter, with
+// int64/double records when the box is 2^30 or more from its centre.
+constexpr int MODE_INT32 = 0, MODE_FP32 = 1, MODE_WIDE = 2;
 
-__device__ __forceinline__ void bar_sync(int id, int n) { asm volatile("bar.sync %0, %1;\n" ::"r"(id), "r"(n) : "memory"); }
-__device__ __forceinline__ void bar_arrive(int id, int n) { asm volatile("bar.arrive %0, %1;\n" ::"r"(id), "r"(n) : "memory"); }
-
-template <typename CI>
-struct __align__(16) PipeStage {
-    int2 v[PM_TV + 2];              // the pass's vertices
-    int2 pts[PM_TC];                // the pass's candidate points
-    CI co[PM_NP + 1];               // candidate offsets of the pass's polygons
-    int po[PM_NP + 1];              // vertex offsets (global)
-    int kind;                       // 0 end, 1 run of small polygons, 2 one large polygon
-    int kg0;                        // global index of the pass's polygon 0
-    int np;                         // polygons in the pass
-    int nc;                         // candidates [cb0, cb0 + nc)
-    CI cb0;
-};
-
-template <typename CI>
-struct __align__(16) PipeSmem {
-    PipeStage<CI> st[2];
-    // consumer-private
-    float4 rec[PM_TV];
-    int4 pbox[PM_NP];
-    int4 pfr[PM_NP];                // ox, oy, bound (float bits), wide
-    unsigned short vp[PM_TV];
-    unsigned short cp[PM_TC];
-    unsigned short queue[PM_TC];
-    unsigned words[PM_TC / 32 + 2];
-    // producer-private
-    int ids[PM_TC];
-    int ppo[PM_NP + 1];
-    CI pco[PM_NP + 1];
-    unsigned plg[PM_NP / 32];
-};
-
-__device__ __forceinline__ bool pm_is_large(long long m, long long n)
+// A polygon goes to k_pip_large when it has more vertices than a run holds or more
+// (candidate, edge) pairs than one warp should walk.
+__device__ __forceinline__ bool is_large_polygon(long long m, long long n)
 {
-    return m > PM_LARGE_M || m * n > PM_LARGE_W;
+    return m > WP_V || m * n > LARGE_W;
 }
+
+struct __align__(16) WarpSmem {
+    float4 rec[WP_V];               // edge records of the run
+    int2 v[WP_V];                   // the run's vertices
+    int4 box[32];                   // per chunk polygon: closed bounding box
+    int4 fr[32];                    // ox, oy, bound (float bits), e0 | e1 << 8 | wide << 16
+    int2 pt[WP_C];                  // candidate points of the slice
+    unsigned char vp[WP_V];         // vertex -> chunk polygon
+    unsigned char sp[WP_C];         // first candidate slot of a polygon -> chunk polygon
+    unsigned char own[WP_C];        // candidate slot -> chunk polygon (0xff: none)
+};
 
 // Sets exactly the bits `mask` of *word to `bits` (other bits untouched, no zero-fill needed).
 __device__ __forceinline__ void masked_store(uint32_t *word, unsigned mask, unsigned bits)
@@ -175,271 +157,260 @@ __device__ __forceinline__ unsigned range_mask(int lo, int hi)   // bits [lo, hi
     return (hi >= 32 ? 0xffffffffu : ((1u << hi) - 1u)) & ~((1u << lo) - 1u);
 }
 
+// Bits [c0, c1) of the output to 0, by the 32 lanes of a warp.
+__device__ __forceinline__ void zero_bits(uint32_t *out, long long c0, long long c1, int lane)
+{
+    if (c1 <= c0) return;
+    const long long w0 = c0 >> 5, w1 = (c1 + 31) >> 5;
+    for (long long wd = w0 + lane; wd < w1; wd += 32) {
+        const int lo = (int)(max(c0, wd * 32) - wd * 32), hi = (int)(min(c1, wd * 32 + 32) - wd * 32);
+        masked_store(out + wd, range_mask(lo, hi), 0u);
+    }
+}
+
 template <bool DENSE>
-__global__ void __launch_bounds__(PM_THREADS, 3) k_pip_pipe(ClassifyArgs a, long long total_bits, LargeList *ll,
-                                                            int lcap)
+__global__ void __launch_bounds__(WP_THREADS, 4) k_pip_warp(ClassifyArgs a, LargeList *ll, int lcap)
 {
     using CI = typename std::conditional<DENSE, long long, int>::type;
     extern __shared__ __align__(16) unsigned char dsm[];
-    PipeSmem<CI> &sm = *reinterpret_cast<PipeSmem<CI> *>(dsm);
-    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    WarpSmem &S = reinterpret_cast<WarpSmem *>(dsm)[threadIdx.x >> 5];
+    const int4 *S_irec = reinterpret_cast<const int4 *>(S.rec);
+    const int lane = threadIdx.x & 31;
     const int P = a.n_polys;
     const CI W32 = (CI)(a.words_per_poly * 32);
-    const CI NPTS = (CI)a.n_points;
-    const int nchunk = (P + PM_NP - 1) / PM_NP;
+    const long long NPTS = a.n_points;
+    const int nchunk = (P + 31) >> 5;
+    const int gw = blockIdx.x * (WP_THREADS / 32) + (threadIdx.x >> 5);
+    const int nw = gridDim.x * (WP_THREADS / 32);
+    unsigned st_cand = 0, st_rej = 0, st_fbp = 0;
+    if (!DENSE && gw == 0 && lane == 0 && P > 0) {
+        // bits past the last candidate in the final word are 0
+        const long long C = __ldg(a.cand_offsets + P);
+        if (C & 31) masked_store(a.out_bits + (C >> 5), ~((1u << (C & 31)) - 1u), 0u);
+    }
 
-    if (wid == 7) {
-        // ================================ producer ================================
-        if (!DENSE && blockIdx.x == 0 && lane == 0 && P > 0) {
-            // bits past the last candidate in the final word are 0
-            const long long C = __ldg(a.cand_offsets + P);
-            if (C & 31) masked_store(a.out_bits + (C >> 5), ~((1u << (C & 31)) - 1u), 0u);
+    for (int ch = gw; ch < nchunk; ch += nw) {
+        // ---- the chunk: polygons k0 + lane, offsets in registers
+        const int k0 = ch << 5, np = min(32, P - k0);
+        const bool has = lane < np;
+        int pb = 0, pe = 0;
+        CI cb = 0, ce = 0;
+        if (has) {
+            pb = __ldg(a.poly_offsets + k0 + lane);
+            pe = __ldg(a.poly_offsets + k0 + lane + 1);
+            if (DENSE) {
+                cb = (CI)(k0 + lane) * W32;
+                ce = cb + W32;
+            } else {
+                cb = __ldg(a.cand_offsets + k0 + lane);
+                ce = __ldg(a.cand_offsets + k0 + lane + 1);
+            }
         }
-        int j = 0;   // pass counter
-        // claim stage j & 1 (after the consumers released pass j - 2)
-        auto begin = [&]() -> PipeStage<CI> & {
-            if (j >= 2) bar_sync(BAR_EMPTY + (j & 1), PM_THREADS);
-            return sm.st[j & 1];
-        };
-        auto publish = [&]() {
-            cp_async_wait_all();
-            __threadfence_block();
-            __syncwarp();
-            bar_arrive(BAR_FULL + (j & 1), PM_THREADS);
-            ++j;
-        };
-        // fill a stage with polygons [p, q) of the chunk and candidates [cb0, cb0 + nc)
-        auto fill = [&](PipeStage<CI> &S, int k0, int p, int q, int kind, CI cb0, int nc) {
-            if (lane == 0) { S.kind = kind; S.kg0 = k0 + p; S.np = q - p; S.nc = nc; S.cb0 = cb0; }
-            for (int t = lane; t <= q - p; t += 32) { S.po[t] = sm.ppo[p + t]; S.co[t] = sm.pco[p + t]; }
-            if (kind != 1) return;
-            const int vb = sm.ppo[p], nv = sm.ppo[q] - vb;
+        const long long nlen = DENSE ? min(NPTS, (long long)W32) : (long long)(ce - cb);
+        const bool lg = has && is_large_polygon(pe - pb, nlen);
+        const unsigned lgm = __ballot_sync(FULL, lg);
+        if (lg && ce > cb && NPTS > 0) {
+            const int idx = atomicAdd(&ll->count, 1);
+            if (idx < lcap) {
+                large_entries(ll)[idx] = k0 + lane;
+                large_taken(ll, lcap)[idx] = 0;
+            } else {
+                atomicExch(&ll->overflow, 1);
+            }
+        }
+        // large polygons' bits are 0 here; k_pip_large XORs their parities in afterwards
+        for (unsigned m = lgm; m; m &= m - 1) {
+            const int l = __ffs(m) - 1;
+            zero_bits(a.out_bits, (long long)__shfl_sync(FULL, cb, l), (long long)__shfl_sync(FULL, ce, l), lane);
+        }
+
+        int p = 0;
+        while (p < np) {
+            if ((lgm >> p) & 1u) { ++p; continue; }
+            // ---- run [p, q): consecutive small polygons with <= WP_V vertices and <= WP_C
+            //      candidates in all; a polygon with more candidates runs alone, in slices
+            const int vb = __shfl_sync(FULL, pb, p);
+            const CI cbp = __shfl_sync(FULL, cb, p);
+            const bool ok = lane >= p && has && !lg && pe - vb <= WP_V && (long long)(ce - cbp) <= WP_C;
+            const unsigned okm = __ballot_sync(FULL, ok) >> p;
+            const int q = p + max(1, __clz(__brev(~okm)));     // trailing ones of okm, at least 1
+            const int nv = __shfl_sync(FULL, pe, q - 1) - vb;
+            const CI cq = __shfl_sync(FULL, ce, q - 1);
+            const bool mine = lane >= p && lane < q;            // this lane's polygon is in the run
+            if (cq <= cbp) { p = q; continue; }                 // no candidates: nothing to write
             for (int i = lane; i < nv; i += 32) cp_async8(&S.v[i], a.verts + vb + i);
-            if (!DENSE) {
-                for (int i = lane; i < nc; i += 32) cp_async4(&sm.ids[i], a.cand_ids + cb0 + i);
-                cp_async_commit();
-                cp_async_wait_all();
+            cp_async_commit();
+            bool staged = false;
+
+            for (CI c0 = cbp; c0 < cq; c0 += WP_C) {
+                const int nc = (int)min((CI)WP_C, cq - c0);
+                // ---- candidate ids of the slice: loads in flight while the owners are found
+                CI pid[WP_R];
+                #pragma unroll
+                for (int r = 0; r < WP_R; ++r) {
+                    const int slot = 32 * r + lane;
+                    pid[r] = -1;
+                    if (!DENSE && slot < nc) pid[r] = __ldg(a.cand_ids + c0 + slot);
+                }
+                // ---- owners of the slots: a polygon whose candidates meet [c0, c0 + nc) marks
+                //      its first slot; slot j belongs to the last mark at or before j
+                int s0 = -1;
+                if (mine && ce > c0 && cb < c0 + nc && ce > cb) {
+                    s0 = (int)(max(cb, c0) - c0);
+                    S.sp[s0] = (unsigned char)lane;
+                }
                 __syncwarp();
-            }
-            for (int i = lane; i < nc; i += 32) {
-                CI pid;
-                if (DENSE) {
-                    const CI c = cb0 + i;
-                    pid = c - (c / W32) * W32;
-                } else {
-                    pid = sm.ids[i];
+                int carry = 0;
+                #pragma unroll 1
+                for (int r = 0; r < WP_R; ++r) {
+                    const unsigned mk = __reduce_or_sync(FULL, (s0 >> 5) == r ? 1u << (s0 & 31) : 0u);
+                    const unsigned below = mk & (0xffffffffu >> (31 - lane));
+                    const int own = below ? (int)S.sp[32 * r + 31 - __clz(below)] : carry;
+                    carry = __shfl_sync(FULL, own, 31);
+                    S.own[32 * r + lane] = (unsigned char)own;
                 }
-                if (pid < NPTS) cp_async8(&S.pts[i], a.points + pid);
-            }
-            cp_async_commit();
-        };
-        for (int ch = blockIdx.x; ch < nchunk; ch += gridDim.x) {
-            const int k0 = ch * PM_NP;
-            const int np = min(PM_NP, P - k0);
-            for (int t = lane; t <= np; t += 32) {
-                cp_async4(&sm.ppo[t], a.poly_offsets + k0 + t);
-                if (!DENSE) cp_async4(&sm.pco[t], a.cand_offsets + k0 + t);
-            }
-            cp_async_commit();
-            cp_async_wait_all();
-            __syncwarp();
-            if (DENSE)
-                for (int t = lane; t <= np; t += 32) sm.pco[t] = (CI)(k0 + t) * W32;
-            __syncwarp();
-            #pragma unroll
-            for (int b = 0; b < PM_NP / 32; ++b) {
-                const int q = 32 * b + lane;
-                bool lg = false;
-                if (q < np) {
-                    const long long n = DENSE ? min((long long)NPTS, (long long)W32) : (long long)(sm.pco[q + 1] - sm.pco[q]);
-                    lg = pm_is_large(sm.ppo[q + 1] - sm.ppo[q], n);
+                // ---- candidate points to shared memory
+                #pragma unroll
+                for (int r = 0; r < WP_R; ++r) {
+                    const int slot = 32 * r + lane;
+                    if (DENSE) {
+                        const CI cbo = __shfl_sync(FULL, cb, S.own[slot]);
+                        if (slot < nc) pid[r] = c0 + slot - cbo;
+                    }
+                    if (pid[r] < 0 || (long long)pid[r] >= NPTS) S.own[slot] = 0xff;   // past the slice, or dense padding
+                    else cp_async8(&S.pt[slot], a.points + pid[r]);
                 }
-                const unsigned m = __ballot_sync(FULL, lg);
-                if (lane == 0) sm.plg[b] = m;
-            }
-            __syncwarp();
-            int p = 0;
-            while (p < np) {
-                if ((sm.plg[p >> 5] >> (p & 31)) & 1u) {
-                    PipeStage<CI> &S = begin();
-                    fill(S, k0, p, p + 1, 2, (CI)sm.pco[p], 0);
-                    publish();
-                    ++p;
-                    continue;
-                }
-                // run [p, q): small polygons, vertices <= PM_TV, candidates <= PM_TC
-                int q = p + 1;
-                for (int base = p + 1; base <= np; base += 32) {
-                    const int e = base + lane;
-                    const bool ok = e <= np && sm.ppo[e] - sm.ppo[p] <= PM_TV &&
-                                    (long long)(sm.pco[e] - sm.pco[p]) <= PM_TC &&
-                                    !((sm.plg[(e - 1) >> 5] >> ((e - 1) & 31)) & 1u);
-                    const unsigned bm = __ballot_sync(FULL, ok);
-                    const int run = bm == FULL ? 32 : __ffs(~bm) - 1;
-                    if (run > 0) q = base + run - 1;
-                    if (run < 32) break;
-                }
-                q = max(q, p + 1);
-                const CI c0 = (CI)sm.pco[p], c1 = (CI)sm.pco[q];
-                if (c1 - c0 <= PM_TC) {
-                    PipeStage<CI> &S = begin();
-                    fill(S, k0, p, q, 1, c0, (int)(c1 - c0));
-                    publish();
-                } else {   // one polygon with more candidates than a pass holds
-                    for (CI cb = c0; cb < c1; cb += PM_TC) {
-                        PipeStage<CI> &S = begin();
-                        fill(S, k0, p, p + 1, 1, cb, (int)min((CI)PM_TC, c1 - cb));
-                        publish();
+                cp_async_commit();
+                if (!staged) {
+                    staged = true;
+                    asm volatile("cp.async.wait_group 1;\n" ::: "memory");     // the vertices
+                    __syncwarp();
+                    // ---- bounding box, frame and arithmetic of each polygon (lane per polygon)
+                    if (mine) {
+                        const int e0 = pb - vb, e1 = pe - vb;
+                        int x0 = INT_MAX, y0 = INT_MAX, x1 = INT_MIN, y1 = INT_MIN;
+                        for (int i = e0; i < e1; ++i) {
+                            const int2 v = S.v[i];
+                            x0 = min(x0, v.x); y0 = min(y0, v.y); x1 = max(x1, v.x); y1 = max(y1, v.y);
+                            S.vp[i] = (unsigned char)lane;
+                        }
+                        const unsigned W = (unsigned)x1 - (unsigned)x0, H = (unsigned)y1 - (unsigned)y0;
+                        const unsigned Mx = W - (W >> 1), My = H - (H >> 1);
+                        int mode, bound = 0;
+                        if (W < (1u << 30) && H < (1u << 30) && (unsigned long long)W * H < (1ULL << 30)) {
+                            mode = MODE_INT32;
+                        } else {
+                            mode = (Mx >= (1u << 30)) | (My >= (1u << 30)) ? MODE_WIDE : MODE_FP32;
+                            bound = __float_as_int(
+                                __fmul_ru(PM_BOUND_K, __fadd_ru(__fmul_ru(__uint2float_ru(Mx), __uint2float_ru(H)),
+                                                                __fmul_ru(__uint2float_ru(My), __uint2float_ru(W)))));
+                        }
+                        S.fr[lane] = make_int4(x0 + (int)(W >> 1), y0 + (int)(H >> 1), bound,
+                                               e0 | (e1 << 8) | (mode << 16));
+                        S.box[lane] = make_int4(x0, y0, x1, y1);
+                    }
+                    __syncwarp();
+                    // ---- edge records, lane per edge
+                    for (int i = lane; i < nv; i += 32) {
+                        const int4 f = S.fr[S.vp[i]];
+                        const int e0 = f.w & 0xff, e1 = (f.w >> 8) & 0xff, mode = f.w >> 16;
+                        const int2 ri = S.v[i], rj = S.v[i + 1 == e1 ? e0 : i + 1];
+                        if (mode == MODE_INT32) {
+                            // exact modulo 2^32; every value the loop forms fits in int32
+                            const unsigned dx = (unsigned)rj.x - (unsigned)ri.x, dy = (unsigned)rj.y - (unsigned)ri.y;
+                            const unsigned X = (unsigned)ri.x - (unsigned)f.x, Y = (unsigned)ri.y - (unsigned)f.y;
+                            const unsigned c = X * dy - Y * dx;
+                            const int Yj = (int)((unsigned)rj.y - (unsigned)f.y);
+                            reinterpret_cast<int4 *>(S.rec)[i] =
+                                (int)dy > 0 ? make_int4((int)(0u - c), (int)dy, (int)(0u - dx), Yj)
+                                            : make_int4((int)c, (int)(0u - dy), (int)dx, Yj);
+                        } else if (mode == MODE_FP32) {
+                            const int dx = rj.x - ri.x, dy = rj.y - ri.y;
+                            const float fdx = __int2float_rn(dx), fdy = __int2float_rn(dy);
+                            const float X = __int2float_rn(ri.x - f.x), Y = __int2float_rn(ri.y - f.y);
+                            const float c = __fmaf_rn(X, fdy, -__fmul_rn(Y, fdx));
+                            S.rec[i] = dy > 0 ? make_float4(c, fdy, fdx, __int_as_float(rj.y))
+                                              : make_float4(-c, -fdy, -fdx, __int_as_float(rj.y));
+                        } else {
+                            S.rec[i] = wide_record(ri, rj, f.x, f.y);
+                        }
                     }
                 }
-                p = q;
+                cp_async_wait_all();
+                __syncwarp();
+                // ---- rounds: one candidate per lane, its polygon's edges in order
+                const int sh = (int)(c0 & 31);
+                unsigned myw = 0;   // lane k assembles word k of the slice
+                #pragma unroll 1
+                for (int r = 0; r < WP_R; ++r) {
+                    const int slot = 32 * r + lane;
+                    const int l = S.own[slot];
+                    int parity = 0;
+                    if (l != 0xff) {
+                        const int2 p2 = S.pt[slot];
+                        const int4 b = S.box[l];
+                        const int4 f = S.fr[l];
+                        const bool in = p2.x >= b.x && p2.x <= b.z && p2.y >= b.y && p2.y <= b.w;
+                        ++st_cand;
+                        st_rej += !in;
+                        const int e0 = f.w & 0xff, e1 = in ? (f.w >> 8) & 0xff : e0;
+                        if (e1 > e0) {
+                            if ((f.w >> 16) == MODE_INT32) {
+                                // nt = -sign(d_y) det exactly; the sign bit of (u_j ^ u_i) is the
+                                // straddle test, u = P_y - Y; count when both sign bits are set
+                                const unsigned Px = (unsigned)p2.x - (unsigned)f.x, Py = (unsigned)p2.y - (unsigned)f.y;
+                                unsigned up = Py - (unsigned)S_irec[e1 - 1].w;   // vertex e0
+                                unsigned acc = 0;
+                                #pragma unroll 4
+                                for (int e = e0; e < e1; ++e) {
+                                    const int4 q4 = S_irec[e];
+                                    const unsigned u = Py - (unsigned)q4.w;
+                                    const unsigned nt = (unsigned)q4.x + Px * (unsigned)q4.y + Py * (unsigned)q4.z;
+                                    acc ^= (u ^ up) & nt;
+                                    up = u;
+                                }
+                                parity = (int)(acc >> 31);
+                            } else {
+                                const int py = p2.y;
+                                const float B = __int_as_float(f.z);
+                                const float Px = __ll2float_rn((long long)p2.x - f.x);
+                                const float Py = __ll2float_rn((long long)p2.y - f.y);
+                                bool sp = S_irec[e1 - 1].w > py;   // vertex e0
+                                bool unc = false;
+                                #pragma unroll 2
+                                for (int e = e0; e < e1; ++e) {
+                                    const float4 q4 = S.rec[e];
+                                    const bool sn = __float_as_int(q4.w) > py;
+                                    const bool st = sn != sp;
+                                    sp = sn;
+                                    float tt = __fmaf_rn(-Px, q4.y, q4.x);
+                                    tt = __fmaf_rn(Py, q4.z, tt);
+                                    parity ^= (int)(st & (tt > 0.f));
+                                    unc |= st & (fabsf(tt) <= B);
+                                }
+                                if (unc) {
+                                    ++st_fbp;
+                                    parity = exact_parity(S.v, e0, e1, true, p2);
+                                }
+                            }
+                        }
+                    }
+                    const unsigned bits = __ballot_sync(FULL, parity);
+                    if (lane == r) myw |= bits << sh;
+                    if (sh && lane == r + 1) myw |= bits >> (32 - sh);
+                }
+                // ---- the slice's words: bits [sh, sh + nc) of words c0 >> 5 ...
+                const int nwd = (sh + nc + 31) >> 5;
+                if (lane < nwd)
+                    masked_store(a.out_bits + (c0 >> 5) + lane,
+                                 range_mask(lane == 0 ? sh : 0, min(32, sh + nc - 32 * lane)), myw);
+                __syncwarp();   // S.sp, S.own and S.pt are rewritten by the next slice
             }
+            p = q;
         }
-        {
-            PipeStage<CI> &S = begin();
-            if (lane == 0) S.kind = 0;
-            publish();
-        }
-        // the consumers' release of the last real pass (j - 2 after the end marker's ++j)
-        if (j >= 2) bar_sync(BAR_EMPTY + (j & 1), PM_THREADS);
-        return;
     }
-
-    // ================================ consumers ================================
-    unsigned st_cand = 0, st_rej = 0, st_fbp = 0;
-    for (int j = 0;; ++j) {
-        bar_sync(BAR_FULL + (j & 1), PM_THREADS);
-        PipeStage<CI> &S = sm.st[j & 1];
-        const int kind = S.kind;
-        if (kind == 0) break;
-        const int np = S.np, nc = S.nc;
-        const CI cb0 = S.cb0;
-        if (kind == 2) {
-            // bits 0 here (k_pip_large XORs the parities in later); the list gets the polygon
-            const CI cbeg = S.co[0], cfin = S.co[1];
-            if (tid == 0 && cfin > cbeg && NPTS > 0) {
-                const int idx = atomicAdd(&ll->count, 1);
-                if (idx < lcap) {
-                    large_entries(ll)[idx] = S.kg0;
-                    large_taken(ll, lcap)[idx] = 0;
-                } else {
-                    atomicExch(&ll->overflow, 1);
-                }
-            }
-            const CI w0 = cbeg >> 5, w1 = (cfin + 31) >> 5;
-            for (CI wd = w0 + tid; wd < w1; wd += PM_CONS) {
-                const int lo = (int)(max(cbeg, wd * 32) - wd * 32), hi = (int)(min(cfin, wd * 32 + 32) - wd * 32);
-                masked_store(a.out_bits + wd, range_mask(lo, hi), 0u);
-            }
-            __threadfence_block();
-            bar_arrive(BAR_EMPTY + (j & 1), PM_THREADS);
-            continue;
-        }
-        const int vbase = S.po[0];
-        const int nv = S.po[np] - vbase;
-        // ---- bounding boxes and frames, one thread per polygon
-        for (int q = tid; q < np; q += PM_CONS) {
-            const int e0 = S.po[q] - vbase, e1 = S.po[q + 1] - vbase;
-            int x0 = INT_MAX, y0 = INT_MAX, x1 = INT_MIN, y1 = INT_MIN;
-            for (int i = e0; i < e1; ++i) {
-                const int2 v = S.v[i];
-                x0 = min(x0, v.x); y0 = min(y0, v.y); x1 = max(x1, v.x); y1 = max(y1, v.y);
-                sm.vp[i] = (unsigned short)q;
-            }
-            const unsigned W = (unsigned)x1 - (unsigned)x0, H = (unsigned)y1 - (unsigned)y0;
-            const unsigned Mx = W - (W >> 1), My = H - (H >> 1);
-            const float B = __fmul_ru(PM_BOUND_K, __fadd_ru(__fmul_ru(__uint2float_ru(Mx), __uint2float_ru(H)),
-                                                             __fmul_ru(__uint2float_ru(My), __uint2float_ru(W))));
-            sm.pfr[q] = make_int4(x0 + (int)(W >> 1), y0 + (int)(H >> 1), __float_as_int(B),
-                                  (Mx >= (1u << 30)) | (My >= (1u << 30)));
-            sm.pbox[q] = make_int4(x0, y0, x1, y1);
-            // candidate slots of this polygon in the pass
-            const int s0 = (int)(max(S.co[q], cb0) - cb0);
-            const int s1 = (int)(min(S.co[q + 1], cb0 + (CI)nc) - cb0);
-            int s1v = s1;
-            if (DENSE) s1v = (int)max((CI)s0, min((CI)s1 + cb0, S.co[q] + NPTS) - cb0);
-            for (int s = s0; s < s1v; ++s) sm.cp[s] = (unsigned short)q;
-            for (int s = s1v; s < s1; ++s) sm.cp[s] = 0xffff;   // dense padding
-        }
-        for (int t = tid; t < PM_TC / 32 + 2; t += PM_CONS) sm.words[t] = 0;
-        bar_sync(BAR_CONS, PM_CONS);
-        // ---- edge records, one thread per edge (FP32 unless the frame is 2^30 wide)
-        for (int i = tid; i < nv; i += PM_CONS) {
-            const int q = sm.vp[i];
-            const int nx = (i + 1 == S.po[q + 1] - vbase) ? S.po[q] - vbase : i + 1;
-            const int2 ri = S.v[i], rj = S.v[nx];
-            const int4 f = sm.pfr[q];
-            float4 rec;
-            if (!f.w) {
-                const int dx = rj.x - ri.x, dy = rj.y - ri.y;
-                const float fdx = __int2float_rn(dx), fdy = __int2float_rn(dy);
-                const float X = __int2float_rn(ri.x - f.x), Y = __int2float_rn(ri.y - f.y);
-                const float c = __fmaf_rn(X, fdy, -__fmul_rn(Y, fdx));
-                rec = dy > 0 ? make_float4(c, fdy, fdx, __int_as_float(rj.y))
-                             : make_float4(-c, -fdy, -fdx, __int_as_float(rj.y));
-            } else {
-                rec = wide_record(ri, rj, f.x, f.y);
-            }
-            sm.rec[i] = rec;
-        }
-        bar_sync(BAR_CONS, PM_CONS);
-        // ---- the edge loop, candidates in order (one per thread): lanes of a warp share one or
-        //      two polygons.  A point outside its polygon's closed box is outside: its y is
-        //      replaced by INT_MAX, so no edge straddles its ray and the loop leaves 0.
-        const int sh = (int)(cb0 & 31);   // bit of candidate cb0 within its word
-        for (int i0 = 0; i0 < nc; i0 += PM_CONS) {   // warp-uniform rounds (ballot below)
-            const int i = i0 + tid;
-            const int q = i < nc ? sm.cp[i] : 0xffff;
-            int parity = 0;
-            if (q != 0xffff) {
-                const int2 p = S.pts[i];
-                const int4 b = sm.pbox[q];
-                const bool in = p.x >= b.x && p.x <= b.z && p.y >= b.y && p.y <= b.w;
-                ++st_cand;
-                st_rej += !in;
-                const int py = in ? p.y : INT_MAX;
-                const int4 f = sm.pfr[q];
-                const int e0 = S.po[q] - vbase, e1 = S.po[q + 1] - vbase;
-                const float B = __int_as_float(f.z);
-                const float Px = __ll2float_rn((long long)p.x - f.x), Py = __ll2float_rn((long long)p.y - f.y);
-                bool sp = S.v[e0].y > py;
-                bool unc = false;
-                #pragma unroll 2
-                for (int e = e0; e < e1; ++e) {
-                    const float4 q4 = sm.rec[e];
-                    const bool sn = __float_as_int(q4.w) > py;
-                    const bool st = sn != sp;
-                    sp = sn;
-                    float tt = __fmaf_rn(-Px, q4.y, q4.x);
-                    tt = __fmaf_rn(Py, q4.z, tt);
-                    parity ^= (int)(st & (tt > 0.f));
-                    unc |= st & (fabsf(tt) <= B);
-                }
-                if (unc) {
-                    ++st_fbp;
-                    parity = exact_parity(S.v, e0, e1, true, p);
-                }
-            }
-            // pack: this warp's 32 consecutive candidates start at bit sh + i0 + 32 wid
-            const unsigned bits = __ballot_sync(FULL, parity);
-            if (lane == 0 && bits) {
-                const int bpos = sh + i0 + 32 * wid;
-                atomicOr(&sm.words[bpos >> 5], bits << (bpos & 31));
-                if (bpos & 31) atomicOr(&sm.words[(bpos >> 5) + 1], bits >> (32 - (bpos & 31)));
-            }
-        }
-        // the stage's data is no longer needed
-        __threadfence_block();
-        bar_arrive(BAR_EMPTY + (j & 1), PM_THREADS);
-        bar_sync(BAR_CONS, PM_CONS);
-        // ---- write the pass's words: bits [sh, sh + nc) of words cb0 >> 5 ...
-        const int nwd = (sh + nc + 31) >> 5;
-        for (int t = tid; t < nwd; t += PM_CONS)
-            masked_store(a.out_bits + (cb0 >> 5) + t, range_mask(t == 0 ? sh : 0, min(32, sh + nc - 32 * t)),
-                         sm.words[t]);
-    }
+    cp_async_wait_all();
     if (a.stats) {
-        st_rej += st_cand;
         #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
             st_cand += __shfl_down_sync(FULL, st_cand, o);
@@ -564,7 +535,7 @@ __global__ void __launch_bounds__(LG_THREADS) k_pip_large(ClassifyArgs a, long l
                     const long long ce = dense ? cs + W32 : (long long)a.cand_offsets[k + 1];
                     const long long m = (long long)a.poly_offsets[k + 1] - a.poly_offsets[k];
                     const long long n = dense ? min((long long)a.n_points, W32) : ce - cs;
-                    const long long nb = pm_is_large(m, n) ? (ce - cs + CB - 1) / CB : 0;
+                    const long long nb = is_large_polygon(m, n) ? (ce - cs + CB - 1) / CB : 0;
                     const int ES = slice_edges(m, nb, count, gridDim.x);
                     const long long ns = (m + ES - 1) / ES;
                     if (scan_item < nb * ns) {
@@ -727,27 +698,26 @@ static int ensure_smem(K kernel, size_t smem, size_t *configured)
 }
 
 template <bool DENSE>
-static int launch_pipe_d(const ClassifyArgs &a, long long total_bits, LargeList *ll, int lcap, int n_sm,
-                         cudaStream_t stream)
+static int launch_warp_d(const ClassifyArgs &a, LargeList *ll, int lcap, int n_sm, cudaStream_t stream)
 {
-    using CI = typename std::conditional<DENSE, long long, int>::type;
     static size_t configured[64] = {0};
     static int blocks_per_sm[64] = {0};
-    const size_t smem = sizeof(PipeSmem<CI>);
-    int e = ensure_smem(k_pip_pipe<DENSE>, smem, configured);
+    const size_t smem = sizeof(WarpSmem) * (WP_THREADS / 32);
+    int e = ensure_smem(k_pip_warp<DENSE>, smem, configured);
     if (e) return e;
     int dev = 0;
     cudaGetDevice(&dev);
     if (dev >= 0 && dev < 64 && blocks_per_sm[dev] == 0) {
         int nb = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_pip_pipe<DENSE>, PM_THREADS, smem) != cudaSuccess)
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_pip_warp<DENSE>, WP_THREADS, smem) != cudaSuccess)
             nb = 1;
         blocks_per_sm[dev] = std::max(nb, 1);
     }
     const int bps = (dev >= 0 && dev < 64) ? blocks_per_sm[dev] : 1;
-    const long long nchunk = ((long long)a.n_polys + PM_NP - 1) / PM_NP;
-    const int grid = (int)std::max(1LL, std::min((long long)n_sm * bps, nchunk));
-    k_pip_pipe<DENSE><<<grid, PM_THREADS, smem, stream>>>(a, total_bits, ll, lcap);
+    const long long nchunk = ((long long)a.n_polys + 31) / 32;
+    const long long need = (nchunk + WP_THREADS / 32 - 1) / (WP_THREADS / 32);
+    const int grid = (int)std::max(1LL, std::min((long long)n_sm * bps, need));
+    k_pip_warp<DENSE><<<grid, WP_THREADS, smem, stream>>>(a, ll, lcap);
     return (int)cudaGetLastError();
 }
 
@@ -766,8 +736,8 @@ static int launch_large_ppt(const ClassifyArgs &a, long long total_bits, LargeLi
 int launch_filtered(const ClassifyArgs &a, long long total_bits, const Tuning &t, int n_sm, LargeList *ll, int lcap,
                     cudaStream_t stream)
 {
-    int e = a.cand_offsets ? launch_pipe_d<false>(a, total_bits, ll, lcap, n_sm, stream)
-                           : launch_pipe_d<true>(a, total_bits, ll, lcap, n_sm, stream);
+    int e = a.cand_offsets ? launch_warp_d<false>(a, ll, lcap, n_sm, stream)
+                           : launch_warp_d<true>(a, ll, lcap, n_sm, stream);
     if (e) return e;
     const int grid = n_sm * t.ctas_per_sm;
     switch (t.pts_per_thread) {

@@ -185,6 +185,25 @@ def test_footprints_scattered_points(api):
     check_full(api, W.scattered_points(W.footprints(seed=21, n_polys=20_000)))
 
 
+def test_filter_statistics(api):
+    """The device counters of the filtered kernel: every candidate is counted once, the box
+    rejects equal a numpy count of candidates outside their polygon's closed bounding box, and
+    the exact rechecks are a subset of the rest."""
+    w = W.footprints(seed=5, n_polys=20_000)
+    api.pip_reset_stats()
+    gpu_bits(api, w)
+    s = api.pip_get_stats()
+    po, v, co, ids = w.poly_offsets.astype(np.int64), w.verts, w.cand_offsets.astype(np.int64), w.cand_ids
+    owner = np.repeat(np.arange(len(po) - 1), np.diff(co))
+    lo = np.stack([np.minimum.reduceat(v[:, k], po[:-1]) for k in (0, 1)], 1)
+    hi = np.stack([np.maximum.reduceat(v[:, k], po[:-1]) for k in (0, 1)], 1)
+    p = w.points[ids]
+    inside = np.all((p >= lo[owner]) & (p <= hi[owner]), axis=1)
+    assert s["candidates"] == w.n_bits
+    assert s["bbox_rejects"] == int((~inside).sum())
+    assert 0 <= s["fallback_points"] <= int(inside.sum())
+
+
 def test_stress_reduced(api):
     check_full(api, W.stress(n_polys=60_000))
 
