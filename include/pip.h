@@ -80,7 +80,7 @@ typedef struct pip_stats {
  * integer arithmetic; otherwise the side test (p - R_i) . n runs in FP32 with a proven
  * forward-error bound, and any candidate with a (point, edge) pair whose FP32 value lies
  * within the bound is re-tested exactly with 64/128-bit integers.  The result is exact
- * either way.  Polygons of up to 128 vertices run in a kernel where each warp takes runs of
+ * either way.  Polygons of up to 256 vertices run in a kernel where each warp takes runs of
  * consecutive polygons; larger ones (or those with more than 2^18 candidate-edge pairs) in
  * a second kernel that splits their edges across CTAs (two launches on `stream`).  The
  * first call on a stream allocates that stream's work list and must not be captured.

@@ -35,16 +35,17 @@
 // Two kernels, launched back to back on the caller's stream:
 //
 // k_pip_warp -- polygon-major, every warp on its own.  A warp takes chunks of 32 consecutive
-//   polygons (lane = polygon, offsets in registers) and cuts each into runs of whole polygons
-//   with at most 128 vertices and 256 candidates; a polygon with more candidates runs alone,
-//   in slices of 256.  Per run it copies the vertices and the candidate points into its own
-//   shared memory (cp.async), finds every candidate's polygon from a bitmap of polygon starts,
-//   forms each polygon's box, frame and arithmetic (lane per polygon) and the edge records
-//   (lane per edge), then classifies the candidates 32 at a time, one per lane, and packs the
-//   parities with ballots.  No barrier spans more than one warp, so the warps of an SM hide
-//   one another's memory latency.  The first and last word of a run may be shared with a
-//   neighbouring run, so those are written with a masked AND/OR pair that sets exactly the
-//   run's own bits (no zero-fill pass is needed).  Polygons with more than 128 vertices or
+//   polygons (lane = polygon, offsets in registers, the next chunk's loaded ahead) and cuts each
+//   into runs of consecutive polygons with at most 256 vertices in all.  Per run it copies the
+//   vertices into its own shared memory (cp.async) and forms the edge records (lane per edge)
+//   and each polygon's box and arithmetic (lane per polygon).  The run's candidates are then
+//   classified in slices of 256: the points are gathered into shared memory (cp.async; the next
+//   slice's ids are loaded ahead), each candidate's polygon is found from a bitmap of polygon
+//   starts, and 32 candidates at a time, one per lane, walk their polygons' edges in lockstep;
+//   ballots pack the parities.  No barrier spans more than one warp, so the warps of an SM hide
+//   one another's memory latency.  The first and last word of a slice may be shared with a
+//   neighbouring slice, so those are written with a masked AND/OR pair that sets exactly the
+//   slice's own bits (no zero-fill pass is needed).  Polygons with more than 256 vertices or
 //   more than 2^18 (candidate, edge) pairs get bit 0 here and go on a device-side list.
 //
 // k_pip_large -- the listed polygons.  Work items (polygon, block of 256*PPT candidates,
@@ -113,8 +114,9 @@ __device__ __noinline__ int exact_parity(const int2 *v, int e0, int e1, bool wra
 // 5u|X d_y| + 6u|Y d_x| + 4u|P_x d_y| + 3u|P_y d_x| (+ O(u^2)) <= 12u (M_x H + M_y W), with H, W
 // the polygon's height and width (>= |d_y|, |d_x| of every edge).
 constexpr float PM_BOUND_K = 7.748603820800781e-07f;     // 13 * 2^-24 (exact in FP32)
-constexpr int WP_THREADS = 256;     // 8 independent warps per CTA
-constexpr int WP_V = 128;           // vertices of a run (and most vertices of a small polygon)
+constexpr int WP_THREADS = 128;     // 4 independent warps per CTA
+constexpr int WP_CTAS = 5;          // CTAs per SM (shared memory: 4 x 9.3 KB per CTA)
+constexpr int WP_V = 256;           // vertices of a run (and most vertices of a small polygon)
 constexpr int WP_R = 8;             // candidate rounds of 32 per run
 constexpr int WP_C = 32 * WP_R;     // candidates of a run
 constexpr long long LARGE_W = 1LL << 18;   // (candidates x vertices) above which a polygon is large
@@ -131,14 +133,13 @@ __device__ __forceinline__ bool is_large_polygon(long long m, long long n)
 }
 
 struct __align__(16) WarpSmem {
-    float4 rec[WP_V];               // edge records of the run
+    float4 rec[WP_V];               // edge records of the run (int32 or FP32, per polygon)
     int2 v[WP_V];                   // the run's vertices
     int4 box[32];                   // per chunk polygon: closed bounding box
-    int4 fr[32];                    // ox, oy, bound (float bits), e0 | e1 << 8 | wide << 16
+    int4 fr[32];                    // ox, oy, bound (float bits), e0 | e1 << 9 | mode << 18
     int2 pt[WP_C];                  // candidate points of the slice
-    unsigned char vp[WP_V];         // vertex -> chunk polygon
+    unsigned vstart[WP_V / 32 + 1]; // bit i: vertex i starts a polygon of the run, or i == nv
     unsigned char sp[WP_C];         // first candidate slot of a polygon -> chunk polygon
-    unsigned char own[WP_C];        // candidate slot -> chunk polygon (0xff: none)
 };
 
 // Sets exactly the bits `mask` of *word to `bits` (other bits untouched, no zero-fill needed).
@@ -168,14 +169,44 @@ __device__ __forceinline__ void zero_bits(uint32_t *out, long long c0, long long
     }
 }
 
+// 16-byte shared-memory load at a 32-bit shared address.
+__device__ __forceinline__ int4 lds128(unsigned addr)
+{
+    int4 v;
+    asm volatile("ld.shared.v4.s32 {%0, %1, %2, %3}, [%4];\n"
+                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "r"(addr));
+    return v;
+}
+
+// Integer record of the edge ri -> rj for the exact int32 test (origin-free):
+// x + p_x y + p_y z = -sign(d_y) det modulo 2^32, w = y_j.
+__device__ __forceinline__ int4 int32_record(int2 ri, int2 rj)
+{
+    const unsigned dx = (unsigned)rj.x - (unsigned)ri.x, dy = (unsigned)rj.y - (unsigned)ri.y;
+    const unsigned c = (unsigned)ri.x * dy - (unsigned)ri.y * dx;
+    return (int)dy > 0 ? make_int4((int)(0u - c), (int)dy, (int)(0u - dx), rj.y)
+                       : make_int4((int)c, (int)(0u - dy), (int)dx, rj.y);
+}
+
+// FP32 record of the edge ri -> rj in the frame with origin (ox, oy) (see PM_BOUND_K).
+__device__ __forceinline__ float4 fp32_record(int2 ri, int2 rj, int ox, int oy)
+{
+    const int dx = rj.x - ri.x, dy = rj.y - ri.y;
+    const float fdx = __int2float_rn(dx), fdy = __int2float_rn(dy);
+    const float X = __int2float_rn(ri.x - ox), Y = __int2float_rn(ri.y - oy);
+    const float c = __fmaf_rn(X, fdy, -__fmul_rn(Y, fdx));
+    return dy > 0 ? make_float4(c, fdy, fdx, __int_as_float(rj.y)) : make_float4(-c, -fdy, -fdx, __int_as_float(rj.y));
+}
+
 template <bool DENSE>
-__global__ void __launch_bounds__(WP_THREADS, 4) k_pip_warp(ClassifyArgs a, LargeList *ll, int lcap)
+__global__ void __launch_bounds__(WP_THREADS, WP_CTAS) k_pip_warp(ClassifyArgs a, LargeList *ll, int lcap)
 {
     using CI = typename std::conditional<DENSE, long long, int>::type;
     extern __shared__ __align__(16) unsigned char dsm[];
     WarpSmem &S = reinterpret_cast<WarpSmem *>(dsm)[threadIdx.x >> 5];
-    const int4 *S_irec = reinterpret_cast<const int4 *>(S.rec);
+    const unsigned rec_base = (unsigned)__cvta_generic_to_shared(S.rec);
     const int lane = threadIdx.x & 31;
+    const unsigned lemask = 0xffffffffu >> (31 - lane);   // lanes 0..lane
     const int P = a.n_polys;
     const CI W32 = (CI)(a.words_per_poly * 32);
     const long long NPTS = a.n_points;
@@ -189,23 +220,36 @@ __global__ void __launch_bounds__(WP_THREADS, 4) k_pip_warp(ClassifyArgs a, Larg
         if (C & 31) masked_store(a.out_bits + (C >> 5), ~((1u << (C & 31)) - 1u), 0u);
     }
 
+    // offsets of a chunk (polygons k0 + lane), loaded one chunk ahead
+    int f_pb = 0, f_pe = 0;
+    CI f_cb = 0, f_ce = 0;
+    auto fetch_chunk = [&](int c) {
+        const int kk = (c << 5) + lane;
+        if (c < nchunk && kk < P) {
+            f_pb = __ldg(a.poly_offsets + kk);
+            f_pe = __ldg(a.poly_offsets + kk + 1);
+            if (DENSE) {
+                f_cb = (CI)kk * W32;
+                f_ce = f_cb + W32;
+            } else {
+                f_cb = __ldg(a.cand_offsets + kk);
+                f_ce = __ldg(a.cand_offsets + kk + 1);
+            }
+        }
+    };
+    // candidate ids of the slice that starts at candidate nid_c0 (CSR), loaded one slice ahead
+    const CI C_total = (!DENSE && P > 0) ? (CI)__ldg(a.cand_offsets + P) : 0;
+    CI nid[WP_R];
+    CI nid_c0 = -1;
+    fetch_chunk(gw);
+
     for (int ch = gw; ch < nchunk; ch += nw) {
         // ---- the chunk: polygons k0 + lane, offsets in registers
         const int k0 = ch << 5, np = min(32, P - k0);
         const bool has = lane < np;
-        int pb = 0, pe = 0;
-        CI cb = 0, ce = 0;
-        if (has) {
-            pb = __ldg(a.poly_offsets + k0 + lane);
-            pe = __ldg(a.poly_offsets + k0 + lane + 1);
-            if (DENSE) {
-                cb = (CI)(k0 + lane) * W32;
-                ce = cb + W32;
-            } else {
-                cb = __ldg(a.cand_offsets + k0 + lane);
-                ce = __ldg(a.cand_offsets + k0 + lane + 1);
-            }
-        }
+        const int pb = has ? f_pb : 0, pe = has ? f_pe : 0;
+        const CI cb = has ? f_cb : 0, ce = has ? f_ce : 0;
+        fetch_chunk(ch + nw);
         const long long nlen = DENSE ? min(NPTS, (long long)W32) : (long long)(ce - cb);
         const bool lg = has && is_large_polygon(pe - pb, nlen);
         const unsigned lgm = __ballot_sync(FULL, lg);
@@ -227,11 +271,11 @@ __global__ void __launch_bounds__(WP_THREADS, 4) k_pip_warp(ClassifyArgs a, Larg
         int p = 0;
         while (p < np) {
             if ((lgm >> p) & 1u) { ++p; continue; }
-            // ---- run [p, q): consecutive small polygons with <= WP_V vertices and <= WP_C
-            //      candidates in all; a polygon with more candidates runs alone, in slices
+            // ---- run [p, q): consecutive small polygons with <= WP_V vertices in all; their
+            //      candidates are classified in slices of WP_C
             const int vb = __shfl_sync(FULL, pb, p);
             const CI cbp = __shfl_sync(FULL, cb, p);
-            const bool ok = lane >= p && has && !lg && pe - vb <= WP_V && (long long)(ce - cbp) <= WP_C;
+            const bool ok = lane >= p && has && !lg && pe - vb <= WP_V;
             const unsigned okm = __ballot_sync(FULL, ok) >> p;
             const int q = p + max(1, __clz(__brev(~okm)));     // trailing ones of okm, at least 1
             const int nv = __shfl_sync(FULL, pe, q - 1) - vb;
@@ -240,171 +284,198 @@ __global__ void __launch_bounds__(WP_THREADS, 4) k_pip_warp(ClassifyArgs a, Larg
             if (cq <= cbp) { p = q; continue; }                 // no candidates: nothing to write
             for (int i = lane; i < nv; i += 32) cp_async8(&S.v[i], a.verts + vb + i);
             cp_async_commit();
+            // vertex i starts a polygon (or i == nv)
+            if (lane <= WP_V / 32) S.vstart[lane] = 0;
+            __syncwarp();
+            if (mine && pe > pb) atomicOr(&S.vstart[(pb - vb) >> 5], 1u << ((pb - vb) & 31));
+            if (lane == 0) atomicOr(&S.vstart[nv >> 5], 1u << (nv & 31));
             bool staged = false;
 
             for (CI c0 = cbp; c0 < cq; c0 += WP_C) {
                 const int nc = (int)min((CI)WP_C, cq - c0);
-                // ---- candidate ids of the slice: loads in flight while the owners are found
+                const CI dbase = DENSE ? (c0 - cbp) % W32 : 0;   // dense: polygon p starts at a multiple of W32
+                // ---- candidate points of the slice to shared memory
                 CI pid[WP_R];
                 #pragma unroll
                 for (int r = 0; r < WP_R; ++r) {
                     const int slot = 32 * r + lane;
                     pid[r] = -1;
-                    if (!DENSE && slot < nc) pid[r] = __ldg(a.cand_ids + c0 + slot);
+                    if (slot < nc) {
+                        if (DENSE) {
+                            CI t = dbase + slot;               // (c0 + slot) mod W32
+                            while (t >= W32) t -= W32;
+                            pid[r] = t;
+                        } else {
+                            pid[r] = c0 == nid_c0 ? nid[r] : (CI)__ldg(a.cand_ids + c0 + slot);
+                        }
+                    }
                 }
-                // ---- owners of the slots: a polygon whose candidates meet [c0, c0 + nc) marks
-                //      its first slot; slot j belongs to the last mark at or before j
-                int s0 = -1;
-                if (mine && ce > c0 && cb < c0 + nc && ce > cb) {
-                    s0 = (int)(max(cb, c0) - c0);
-                    S.sp[s0] = (unsigned char)lane;
-                }
-                __syncwarp();
-                int carry = 0;
-                #pragma unroll 1
-                for (int r = 0; r < WP_R; ++r) {
-                    const unsigned mk = __reduce_or_sync(FULL, (s0 >> 5) == r ? 1u << (s0 & 31) : 0u);
-                    const unsigned below = mk & (0xffffffffu >> (31 - lane));
-                    const int own = below ? (int)S.sp[32 * r + 31 - __clz(below)] : carry;
-                    carry = __shfl_sync(FULL, own, 31);
-                    S.own[32 * r + lane] = (unsigned char)own;
-                }
-                // ---- candidate points to shared memory
+                unsigned validm = 0;
                 #pragma unroll
                 for (int r = 0; r < WP_R; ++r) {
-                    const int slot = 32 * r + lane;
-                    if (DENSE) {
-                        const CI cbo = __shfl_sync(FULL, cb, S.own[slot]);
-                        if (slot < nc) pid[r] = c0 + slot - cbo;
+                    if (pid[r] >= 0 && (long long)pid[r] < NPTS) {   // else past the slice, or dense padding
+                        cp_async8(&S.pt[32 * r + lane], a.points + pid[r]);
+                        validm |= 1u << r;
                     }
-                    if (pid[r] < 0 || (long long)pid[r] >= NPTS) S.own[slot] = 0xff;   // past the slice, or dense padding
-                    else cp_async8(&S.pt[slot], a.points + pid[r]);
                 }
                 cp_async_commit();
+                if (!DENSE) {   // the ids of the candidates that follow, for the next slice
+                    nid_c0 = c0 + nc;
+                    #pragma unroll
+                    for (int r = 0; r < WP_R; ++r) {
+                        const CI c = nid_c0 + 32 * r + lane;
+                        nid[r] = c < C_total ? (CI)__ldg(a.cand_ids + c) : (CI)-1;
+                    }
+                }
+                // ---- owners: a polygon whose candidates meet [c0, c0 + nc) marks its first slot;
+                //      slot j belongs to the last mark at or before j
+                int sword = -1;
+                unsigned sbit = 0;
+                if (mine && ce > c0 && cb < c0 + nc && ce > cb) {
+                    const int s0 = (int)(max(cb, c0) - c0);
+                    S.sp[s0] = (unsigned char)lane;
+                    sword = s0 >> 5;
+                    sbit = 1u << (s0 & 31);
+                }
                 if (!staged) {
                     staged = true;
                     asm volatile("cp.async.wait_group 1;\n" ::: "memory");     // the vertices
                     __syncwarp();
-                    // ---- bounding box, frame and arithmetic of each polygon (lane per polygon)
+                    // ---- int32 records of the edges that do not close their polygon (lane per edge)
+                    for (int i = lane; i + 1 < nv; i += 32)
+                        if (!((S.vstart[(i + 1) >> 5] >> ((i + 1) & 31)) & 1u)) {
+                            const int4 r4 = int32_record(S.v[i], S.v[i + 1]);
+                            S.rec[i] = make_float4(__int_as_float(r4.x), __int_as_float(r4.y), __int_as_float(r4.z),
+                                                   __int_as_float(r4.w));
+                        }
+                    __syncwarp();
+                    // ---- per polygon (lane per polygon): box, arithmetic mode, closing edge; all of
+                    //      its records in FP32 when the box is too large for the int32 test
                     if (mine) {
                         const int e0 = pb - vb, e1 = pe - vb;
                         int x0 = INT_MAX, y0 = INT_MAX, x1 = INT_MIN, y1 = INT_MIN;
+                        #pragma unroll 2
                         for (int i = e0; i < e1; ++i) {
                             const int2 v = S.v[i];
                             x0 = min(x0, v.x); y0 = min(y0, v.y); x1 = max(x1, v.x); y1 = max(y1, v.y);
-                            S.vp[i] = (unsigned char)lane;
                         }
                         const unsigned W = (unsigned)x1 - (unsigned)x0, H = (unsigned)y1 - (unsigned)y0;
                         const unsigned Mx = W - (W >> 1), My = H - (H >> 1);
-                        int mode, bound = 0;
-                        if (W < (1u << 30) && H < (1u << 30) && (unsigned long long)W * H < (1ULL << 30)) {
-                            mode = MODE_INT32;
-                        } else {
+                        const int ox = x0 + (int)(W >> 1), oy = y0 + (int)(H >> 1);
+                        int mode = MODE_INT32, bound = 0;
+                        if (!(W < (1u << 30) && H < (1u << 30) && (unsigned long long)W * H < (1ULL << 30))) {
                             mode = (Mx >= (1u << 30)) | (My >= (1u << 30)) ? MODE_WIDE : MODE_FP32;
                             bound = __float_as_int(
                                 __fmul_ru(PM_BOUND_K, __fadd_ru(__fmul_ru(__uint2float_ru(Mx), __uint2float_ru(H)),
                                                                 __fmul_ru(__uint2float_ru(My), __uint2float_ru(W)))));
                         }
-                        S.fr[lane] = make_int4(x0 + (int)(W >> 1), y0 + (int)(H >> 1), bound,
-                                               e0 | (e1 << 8) | (mode << 16));
+                        S.fr[lane] = make_int4(ox, oy, bound, e0 | (e1 << 9) | (mode << 18));
                         S.box[lane] = make_int4(x0, y0, x1, y1);
-                    }
-                    __syncwarp();
-                    // ---- edge records, lane per edge
-                    for (int i = lane; i < nv; i += 32) {
-                        const int4 f = S.fr[S.vp[i]];
-                        const int e0 = f.w & 0xff, e1 = (f.w >> 8) & 0xff, mode = f.w >> 16;
-                        const int2 ri = S.v[i], rj = S.v[i + 1 == e1 ? e0 : i + 1];
-                        if (mode == MODE_INT32) {
-                            // exact modulo 2^32; every value the loop forms fits in int32
-                            const unsigned dx = (unsigned)rj.x - (unsigned)ri.x, dy = (unsigned)rj.y - (unsigned)ri.y;
-                            const unsigned X = (unsigned)ri.x - (unsigned)f.x, Y = (unsigned)ri.y - (unsigned)f.y;
-                            const unsigned c = X * dy - Y * dx;
-                            const int Yj = (int)((unsigned)rj.y - (unsigned)f.y);
-                            reinterpret_cast<int4 *>(S.rec)[i] =
-                                (int)dy > 0 ? make_int4((int)(0u - c), (int)dy, (int)(0u - dx), Yj)
-                                            : make_int4((int)c, (int)(0u - dy), (int)dx, Yj);
-                        } else if (mode == MODE_FP32) {
-                            const int dx = rj.x - ri.x, dy = rj.y - ri.y;
-                            const float fdx = __int2float_rn(dx), fdy = __int2float_rn(dy);
-                            const float X = __int2float_rn(ri.x - f.x), Y = __int2float_rn(ri.y - f.y);
-                            const float c = __fmaf_rn(X, fdy, -__fmul_rn(Y, fdx));
-                            S.rec[i] = dy > 0 ? make_float4(c, fdy, fdx, __int_as_float(rj.y))
-                                              : make_float4(-c, -fdy, -fdx, __int_as_float(rj.y));
-                        } else {
-                            S.rec[i] = wide_record(ri, rj, f.x, f.y);
+                        if (e1 > e0) {
+                            if (mode == MODE_INT32) {
+                                const int4 r4 = int32_record(S.v[e1 - 1], S.v[e0]);
+                                S.rec[e1 - 1] = make_float4(__int_as_float(r4.x), __int_as_float(r4.y),
+                                                            __int_as_float(r4.z), __int_as_float(r4.w));
+                            } else {
+                                for (int i = e0; i < e1; ++i) {
+                                    const int2 ri = S.v[i], rj = S.v[i + 1 == e1 ? e0 : i + 1];
+                                    S.rec[i] = mode == MODE_FP32 ? fp32_record(ri, rj, ox, oy) : wide_record(ri, rj, ox, oy);
+                                }
+                            }
                         }
                     }
                 }
                 cp_async_wait_all();
                 __syncwarp();
-                // ---- rounds: one candidate per lane, its polygon's edges in order
+                // ---- rounds: one candidate per lane; the lanes of a warp walk their polygons'
+                //      edges in lockstep, a lane whose polygon has fewer edges repeating its last
+                //      record (a repeated edge never straddles, so it adds nothing)
                 const int sh = (int)(c0 & 31);
-                unsigned myw = 0;   // lane k assembles word k of the slice
+                unsigned mybits = 0;   // lane r keeps the ballot of round r
+                int carry = 0;
+                const int nr = (nc + 31) >> 5;
                 #pragma unroll 1
-                for (int r = 0; r < WP_R; ++r) {
-                    const int slot = 32 * r + lane;
-                    const int l = S.own[slot];
+                for (int r = 0; r < nr; ++r) {
+                    const unsigned mk = __reduce_or_sync(FULL, sword == r ? sbit : 0u);
+                    const unsigned below = mk & lemask;
+                    const int own = below ? (int)S.sp[32 * r + 31 - __clz(below)] : carry;
+                    carry = __shfl_sync(FULL, own, 31);
+                    const bool valid = (validm >> r) & 1u;
+                    const int2 p2 = S.pt[32 * r + lane];
+                    const int4 b = S.box[own];
+                    const int4 f = S.fr[own];
+                    const bool in = valid && p2.x >= b.x && p2.x <= b.z && p2.y >= b.y && p2.y <= b.w;
+                    st_cand += valid;
+                    st_rej += valid && !in;
+                    const int e0 = f.w & 0x1ff, e1 = (f.w >> 9) & 0x1ff, mode = f.w >> 18;
+                    const bool go = in && e1 > e0;
                     int parity = 0;
-                    if (l != 0xff) {
-                        const int2 p2 = S.pt[slot];
-                        const int4 b = S.box[l];
-                        const int4 f = S.fr[l];
-                        const bool in = p2.x >= b.x && p2.x <= b.z && p2.y >= b.y && p2.y <= b.w;
-                        ++st_cand;
-                        st_rej += !in;
-                        const int e0 = f.w & 0xff, e1 = in ? (f.w >> 8) & 0xff : e0;
-                        if (e1 > e0) {
-                            if ((f.w >> 16) == MODE_INT32) {
-                                // nt = -sign(d_y) det exactly; the sign bit of (u_j ^ u_i) is the
-                                // straddle test, u = P_y - Y; count when both sign bits are set
-                                const unsigned Px = (unsigned)p2.x - (unsigned)f.x, Py = (unsigned)p2.y - (unsigned)f.y;
-                                unsigned up = Py - (unsigned)S_irec[e1 - 1].w;   // vertex e0
-                                unsigned acc = 0;
-                                #pragma unroll 4
-                                for (int e = e0; e < e1; ++e) {
-                                    const int4 q4 = S_irec[e];
-                                    const unsigned u = Py - (unsigned)q4.w;
-                                    const unsigned nt = (unsigned)q4.x + Px * (unsigned)q4.y + Py * (unsigned)q4.z;
-                                    acc ^= (u ^ up) & nt;
-                                    up = u;
-                                }
-                                parity = (int)(acc >> 31);
-                            } else {
-                                const int py = p2.y;
-                                const float B = __int_as_float(f.z);
-                                const float Px = __ll2float_rn((long long)p2.x - f.x);
-                                const float Py = __ll2float_rn((long long)p2.y - f.y);
-                                bool sp = S_irec[e1 - 1].w > py;   // vertex e0
-                                bool unc = false;
-                                #pragma unroll 2
-                                for (int e = e0; e < e1; ++e) {
-                                    const float4 q4 = S.rec[e];
-                                    const bool sn = __float_as_int(q4.w) > py;
-                                    const bool st = sn != sp;
-                                    sp = sn;
-                                    float tt = __fmaf_rn(-Px, q4.y, q4.x);
-                                    tt = __fmaf_rn(Py, q4.z, tt);
-                                    parity ^= (int)(st & (tt > 0.f));
-                                    unc |= st & (fabsf(tt) <= B);
-                                }
-                                if (unc) {
-                                    ++st_fbp;
-                                    parity = exact_parity(S.v, e0, e1, true, p2);
-                                }
+                    const bool gi = go && mode == MODE_INT32;
+                    const int ki = __reduce_max_sync(FULL, gi ? e1 - e0 : 0);
+                    if (ki > 0) {
+                        // nt = -sign(d_y) det exactly; the sign bit of (u_j ^ u_i) is the straddle
+                        // test, u = p_y - y; a crossing counts when both sign bits are set
+                        unsigned ad = rec_base + 16u * (unsigned)(gi ? e0 : 0);
+                        const unsigned al = rec_base + 16u * (unsigned)(gi ? e1 - 1 : 0);
+                        const unsigned px = (unsigned)p2.x, py = (unsigned)p2.y;
+                        unsigned up = py - (unsigned)lds128(al).w;   // vertex e0
+                        unsigned acc = 0;
+                        #pragma unroll 4
+                        for (int k = 0; k < ki; ++k) {
+                            const int4 q4 = lds128(ad);
+                            ad = __viaddmin_u32(ad, 16u, al);
+                            const unsigned u = py - (unsigned)q4.w;
+                            const unsigned nt = (unsigned)q4.x + px * (unsigned)q4.y + py * (unsigned)q4.z;
+                            acc ^= (u ^ up) & nt;
+                            up = u;
+                        }
+                        parity = (int)(acc >> 31);
+                    }
+                    const bool gf = go && mode != MODE_INT32;
+                    const int kf = __reduce_max_sync(FULL, gf ? e1 - e0 : 0);
+                    if (kf > 0) {
+                        unsigned ad = rec_base + 16u * (unsigned)(gf ? e0 : 0);
+                        const unsigned al = rec_base + 16u * (unsigned)(gf ? e1 - 1 : 0);
+                        const int py = p2.y;
+                        const float B = __int_as_float(f.z);
+                        const float Px = __ll2float_rn((long long)p2.x - f.x);
+                        const float Py = __ll2float_rn((long long)p2.y - f.y);
+                        bool sp = lds128(al).w > py;   // vertex e0
+                        bool unc = false;
+                        int par = 0;
+                        #pragma unroll 2
+                        for (int k = 0; k < kf; ++k) {
+                            const int4 q4 = lds128(ad);
+                            ad = __viaddmin_u32(ad, 16u, al);
+                            const bool sn = q4.w > py;
+                            const bool st = sn != sp;
+                            sp = sn;
+                            float tt = __fmaf_rn(-Px, __int_as_float(q4.y), __int_as_float(q4.x));
+                            tt = __fmaf_rn(Py, __int_as_float(q4.z), tt);
+                            par ^= (int)(st & (tt > 0.f));
+                            unc |= st & (fabsf(tt) <= B);
+                        }
+                        if (gf) {
+                            parity = par;
+                            if (unc) {
+                                ++st_fbp;
+                                parity = exact_parity(S.v, e0, e1, true, p2);
                             }
                         }
                     }
                     const unsigned bits = __ballot_sync(FULL, parity);
-                    if (lane == r) myw |= bits << sh;
-                    if (sh && lane == r + 1) myw |= bits >> (32 - sh);
+                    if (lane == r) mybits = bits;
                 }
-                // ---- the slice's words: bits [sh, sh + nc) of words c0 >> 5 ...
+                // ---- the slice's words: word k = bits_k << sh | bits_(k-1) >> (32 - sh), of which
+                //      bits [sh, sh + nc) of words c0 >> 5 ... belong to the slice
+                const unsigned prev = __shfl_up_sync(FULL, mybits, 1);
+                unsigned myw = mybits << sh;
+                if (sh && lane > 0) myw |= prev >> (32 - sh);
                 const int nwd = (sh + nc + 31) >> 5;
                 if (lane < nwd)
                     masked_store(a.out_bits + (c0 >> 5) + lane,
                                  range_mask(lane == 0 ? sh : 0, min(32, sh + nc - 32 * lane)), myw);
-                __syncwarp();   // S.sp, S.own and S.pt are rewritten by the next slice
+                __syncwarp();   // S.sp and S.pt are rewritten by the next slice
             }
             p = q;
         }
