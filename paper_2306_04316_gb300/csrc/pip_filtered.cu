@@ -575,6 +575,7 @@ __global__ void __launch_bounds__(LG_THREADS) k_pip_large(ClassifyArgs a, long l
     unsigned long long st_cand = 0, st_fbp = 0;
     const int count = *((volatile int *)&ll->count);
     const bool scan = *((volatile int *)&ll->overflow) != 0;
+    if (count == 0 && !scan) return;   // nothing listed: the header is already clear for the next call
     long long scan_k = blockIdx.x;   // overflow mode: polygons blockIdx.x, + gridDim.x, ...
     int scan_item = 0;
 
