@@ -44,6 +44,41 @@ def _env_int(k, d):
         return d
 
 
+def dist_setup(world, backend="nccl"):
+    """torch.distributed for N > 1 (one process per GPU, launched by torchrun), else None."""
+    if world <= 1:
+        return None
+    import torch.distributed as dist
+    if not dist.is_initialized():
+        dist.init_process_group(backend)
+    return dist
+
+
+def max_over_ranks(dist, value, device="cuda"):
+    """The largest value over all ranks (the job's time is its slowest rank's)."""
+    if dist is None:
+        return float(value)
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(dist, value, device="cuda"):
+    """The total of a per-rank count over all ranks (each rank's batch has its own data)."""
+    if dist is None:
+        return float(value)
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def job_rate(units_all_ranks, ms):
+    """Whole-job throughput: the units all ranks processed over the slowest rank's time."""
+    return units_all_ranks / (ms / 1000.0)
+
+
 def measured_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -246,6 +281,7 @@ def run_join(args, rank, world):
 
     pbuild.build_library()
     torch.cuda.set_device(_env_int("LOCAL_RANK", 0))
+    dist = dist_setup(world)
     nb = args.batches
     n_pts = int(10_000_000 * args.scale)
     seed = W.BASE_SEED + 3 + 1000 * rank
@@ -284,11 +320,13 @@ def run_join(args, rank, world):
     m = np.diff(po.astype(np.int64))
     T = sum(int((m * np.diff(c.cpu().numpy().astype(np.int64))).sum()) for c in co)
     C = sum(int(c[-1].item()) for c in co)
-    graphs = {}
+    graphs, per_replay = {}, {}
     for name, cls in (("full", True), ("binning", False)):
         g = torch.cuda.CUDAGraph()
+        l0 = api.pip_launch_count()
         with torch.cuda.graph(g, stream=stream):
             one_pass(cls)
+        per_replay[name] = api.pip_launch_count() - l0
         graphs[name] = g
     res = {}
     for name, g in graphs.items():
@@ -300,16 +338,31 @@ def run_join(args, rank, world):
         sampler = ClockSampler(_env_int("LOCAL_RANK", 0)) if name == "full" else None
         if sampler:
             sampler.start()
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
         e0.record(stream)
         with torch.cuda.stream(stream):
             for _ in range(args.steps):
                 g.replay()
         e1.record(stream)
         stream.synchronize()
-        res[name] = (e0.elapsed_time(e1) / args.steps, sampler.stop() if sampler else None)
+        if dist:
+            dist.barrier()
+        res[name] = (max_over_ranks(dist, e0.elapsed_time(e1)) / args.steps, sampler.stop() if sampler else None)
     ms, clocks = res["full"]
+    T_all = sum_over_ranks(dist, T)
     bin_ms = res["binning"][0]
-    bin_bytes = nb * (n_pts * 8 * 3 + n_pts * 4 * 2 * 2 * 3 + P * 16)   # rough: reads/writes of the passes
+    # algorithmic bytes of a step: per batch, binning reads the points twice (bounds, keys) and
+    # gathers them once in cell order, sorts (key, id) pairs in three radix passes (read and
+    # write 8 B each), reads the polygons' vertices for their boxes and writes the CSR; the
+    # classification reads vertices, offsets, ids and points and writes the bits
+    V = int(po[-1])
+    classify_bytes = 8 * V * nb + 8 * (P + 1) * nb + 12 * C + C // 8
+    bin_bytes = nb * (3 * 8 * n_pts + 3 * 2 * 8 * n_pts + 8 * V + 4 * (P + 1)) + 4 * C
+    join_bytes = classify_bytes + bin_bytes
+    peaks, peak_kind = measured_peaks()
+    hbm = float(peaks["hbm_gbs"])
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         sub_p = min(P, 2000)
@@ -318,16 +371,23 @@ def run_join(args, rank, world):
         cpu = oracle_baseline(sub.with_csr(co_s, ids_s, name="join-sample"))
         cpu["sample"] = f"first {sub_p} polygons x first 1M points of batch 0 (numpy closed-bbox CSR): " + cpu["sample"]
     if rank == 0:
-        line = {"metric": METRIC, "value": T / (ms / 1000.0), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        line = {"metric": METRIC, "value": job_rate(T_all, ms), "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f32+i64", "data": "synthetic",
                 "config": {"workload": f"join: {P} polygons x {nb} batches of {n_pts} clustered points, "
                                        f"{C} candidates from GPU binning, one CUDA-graph replay per step",
                            "pair_tests_per_step": T, "candidates_per_step": C, "binning_ms_per_step": bin_ms,
                            "classify_ms_per_step": ms - bin_ms, "l2": "inputs larger than L2 (no flush)"},
-                "points_per_s": nb * n_pts / (ms / 1000.0), "cpu_baseline": cpu, "clocks": clocks,
-                "gpu_launches": None, "roofline": None, "e2e": None}
+                "points_per_s": job_rate(nb * n_pts * world, ms), "cpu_baseline": cpu, "clocks": clocks,
+                "gpu_launches": per_replay["full"] * args.steps,
+                "roofline": {"bound": "hbm", "achieved": join_bytes / (ms / 1000.0) / 1e9, "peak": hbm,
+                             "unit": "GB/s", "frac": join_bytes / (ms / 1000.0) / 1e9 / hbm, "traffic": None,
+                             "peak_source": peak_kind, "kernel": "binning + k_pip_warp + k_pip_large (whole step)",
+                             "algorithmic_bytes": join_bytes, "kernel_ms": ms},
+                "e2e": None}
         print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
     return 0
 
 
@@ -364,10 +424,7 @@ def main():
     torch.cuda.set_device(local)
     if args.tuning:
         api.pip_set_tuning(*[int(x) for x in args.tuning.split(",")])
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl")
+    dist = dist_setup(world)
 
     w = make_workload(args.workload, rank, args.scale)
     T = w.pair_tests()
@@ -393,20 +450,21 @@ def main():
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
+    launches0 = api.pip_launch_count()
     for i in range(args.steps):
         ev0[i].record(stream)
         step()
         ev1[i].record(stream)
+    launches = api.pip_launch_count() - launches0
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
     clocks = sampler.stop()
     per = [ev0[i].elapsed_time(ev1[i]) for i in range(args.steps)]
     total_ms = ev0[0].elapsed_time(ev1[-1])
-    t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
-    if dist:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    total_ms = float(t.item())
+    total_ms = max_over_ranks(dist, total_ms)
+    T_all = sum_over_ranks(dist, T)
+    C_all = sum_over_ranks(dist, w.n_candidates)
     ms_step = total_ms / args.steps
     kern_ms = statistics.mean(per)
 
@@ -454,11 +512,8 @@ def main():
             e2e_step()
         e1.record(stream)
         torch.cuda.synchronize()
-        te = torch.tensor([e0.elapsed_time(e1)], dtype=torch.float64, device="cuda")
-        if dist:
-            dist.all_reduce(te, op=dist.ReduceOp.MAX)
-        e2e_ms = float(te.item()) / args.e2e_steps
-        e2e = {"value": T * world / (e2e_ms / 1000.0), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+        e2e_ms = max_over_ranks(dist, e0.elapsed_time(e1)) / args.e2e_steps
+        e2e = {"value": job_rate(T_all, e2e_ms), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(d2h), "ms_per_step": e2e_ms}
 
     peaks, peak_kind = measured_peaks()
@@ -491,7 +546,7 @@ def main():
     if rank == 0:
         stats = api.pip_get_stats()
         line = {
-            "metric": METRIC, "value": T * world / (ms_step / 1000.0), "unit": UNIT, "n_gpus": world,
+            "metric": METRIC, "value": job_rate(T_all, ms_step), "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32+i64" if args.kernel == "filtered" else "i64",
             "data": "synthetic",
@@ -499,11 +554,11 @@ def main():
                                    f"{w.verts.shape[0]} vertices", "pair_tests_per_step": T,
                        "algorithmic_bytes_per_step": B, "kernel": args.kernel,
                        "tuning": list(api.pip_get_tuning()), "l2": "inputs larger than L2 (no flush)"},
-            "points_per_s": w.n_candidates * world / (ms_step / 1000.0),
+            "points_per_s": job_rate(C_all, ms_step),
             "roofline": roof,
             "cpu_baseline": cpu,
             "e2e": e2e,
-            "gpu_launches": args.steps * (2 if args.kernel == "filtered" else 1),
+            "gpu_launches": launches,
             "clocks": clocks,
             "other_kernel": {"kernel": "exact" if args.kernel == "filtered" else "filtered",
                              "ms_per_step": other_ms,

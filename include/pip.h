@@ -197,6 +197,13 @@ int pip_last_cuda_error(void);
 /* ABI version (major * 100 + minor). */
 int pip_version(void);
 
+/*
+ * Number of CUDA kernels the library has enqueued since it was loaded, over all calls,
+ * devices and threads (not in the paper; for launch accounting).  A launch recorded into a
+ * CUDA graph during stream capture counts once, at capture, not at each replay.
+ */
+uint64_t pip_launch_count(void);
+
 #ifdef __cplusplus
 }
 #endif

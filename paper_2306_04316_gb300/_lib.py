@@ -63,6 +63,7 @@ _SIGS = {
     "pip_status_str": ([ctypes.c_int], ctypes.c_char_p),
     "pip_last_cuda_error": ([], ctypes.c_int),
     "pip_version": ([], ctypes.c_int),
+    "pip_launch_count": ([], ctypes.c_uint64),
 }
 
 

@@ -15,7 +15,7 @@ import torch
 from . import _lib
 
 __all__ = ["pip_classify", "pip_classify_exact", "pip_classify_noalloc", "pip_bin_count", "pip_bin_fill", "bin_join",
-           "pip_set_tuning", "pip_get_tuning", "pip_get_stats", "pip_reset_stats", "pip_validate",
+           "pip_set_tuning", "pip_get_tuning", "pip_get_stats", "pip_reset_stats", "pip_launch_count", "pip_validate",
            "out_words", "to_device"]
 
 
@@ -163,6 +163,11 @@ def pip_get_stats() -> dict:
     s = _lib.PipStats()
     _lib.check("pip_get_stats", _lib.load().pip_get_stats(ctypes.byref(s)))
     return {f: int(getattr(s, f)) for f, _ in _lib.PipStats._fields_}
+
+
+def pip_launch_count() -> int:
+    """Kernels the library has enqueued since it was loaded (graph replays not counted)."""
+    return int(_lib.load().pip_launch_count())
 
 
 def pip_reset_stats():

@@ -135,12 +135,15 @@ static int scan_exclusive(unsigned *d, long long n, unsigned *tmp, cudaStream_t 
     const long long nb = (n + SCAN_TILE - 1) / SCAN_TILE;
     if (nb <= 1) {
         k_scan_block<<<1, 256, 0, s>>>(d, n, nullptr);
+        note_launch();
         return (int)cudaGetLastError();
     }
     k_scan_block<<<(unsigned)nb, 256, 0, s>>>(d, n, tmp);
+    note_launch();
     int e = scan_exclusive(tmp, nb, tmp + nb, s);
     if (e) return e;
     k_scan_add<<<(unsigned)nb, 256, 0, s>>>(d, n, tmp);
+    note_launch();
     return (int)cudaGetLastError();
 }
 
@@ -466,31 +469,38 @@ int launch_bin_count(const int2 *points, long long N, const int32_t *po, const i
     if (P > 0) k_poly_bbox<<<grid, 256, 0, s>>>(po, verts, P, bb, h);
     if (N > 0) k_points_bbox<<<grid, 256, 0, s>>>(points, N, h);
     k_grid_params<<<1, 32, 0, s>>>(h);
+    note_launch(2 + (P > 0) + (N > 0));
     if ((e = (int)cudaMemsetAsync(cstart, 0, (size_t)(BIN_MAX_CELLS + 1) * 4, s))) return e;
     if (N > 0) {
         k_point_keys<<<grid, 256, 0, s>>>(points, N, h, ka, va, cstart);
+        note_launch();
         if ((e = scan_exclusive(cstart, BIN_MAX_CELLS + 1, tmp, s))) return e;
         const int nblk = (int)((N + RADIX_TILE - 1) / RADIX_TILE);
         const int shifts[3] = {0, 8, 16};
         for (int pass = 0; pass < 3; ++pass) {
             k_radix_hist<<<nblk, RADIX_THREADS, 0, s>>>(ka, N, shifts[pass], nblk, hist);
+            note_launch();
             if ((e = scan_exclusive(hist, 256LL * nblk, tmp, s))) return e;
             k_radix_scatter<<<nblk, RADIX_THREADS, 0, s>>>(ka, va, kb, vb, N, shifts[pass], nblk, hist);
+            note_launch();
             std::swap(ka, kb);
             std::swap(va, vb);
         }
         // after three passes the sorted ids are in the buffer that started as vals_b
         k_gather_sorted<<<grid, 256, 0, s>>>(points, va, N, spts);
+        note_launch();
     }
     if (P > 0) {
         k_poly_candidates<false><<<grid, 256, 0, s>>>(bb, po, P, h, cstart, spts, va,
                                                       reinterpret_cast<unsigned *>(cand_offsets), nullptr,
                                                       nullptr, 0, d_total);
+        note_launch();
         if ((e = scan_exclusive(reinterpret_cast<unsigned *>(cand_offsets), (long long)P + 1, tmp, s))) return e;
     } else {
         if ((e = (int)cudaMemsetAsync(cand_offsets, 0, 4, s))) return e;
     }
     k_bin_finish<<<1, 32, 0, s>>>(h, d_total, cand_offsets, P, 0, nullptr);
+    note_launch();
     return (int)cudaGetLastError();
 }
 
@@ -508,10 +518,13 @@ int launch_bin_fill(const int2 *points, long long N, const int32_t *po, const in
     const int2 *spts = reinterpret_cast<const int2 *>(w + L.spts);
     const unsigned *cstart = reinterpret_cast<const unsigned *>(w + L.cell_start);
     const int grid = n_sm * 8;
-    if (P > 0 && N > 0)
+    if (P > 0 && N > 0) {
         k_poly_candidates<true><<<grid, 256, 0, s>>>(bb, po, P, h, cstart, spts, sids, nullptr, cand_offsets,
                                                      cand_ids, capacity, nullptr);
+        note_launch();
+    }
     k_bin_finish<<<1, 32, 0, s>>>(h, nullptr, cand_offsets, P, capacity, d_overflow);
+    note_launch();
     return (int)cudaGetLastError();
 }
 

@@ -28,6 +28,7 @@ DeviceState g_dev[MAX_DEVICES];
 std::atomic<int> g_edge_tile{2048};
 std::atomic<int> g_ctas{4};
 std::atomic<int> g_ppt{2};
+std::atomic<unsigned long long> g_launches{0};
 thread_local int g_last_cuda = 0;
 
 int cuda_fail(cudaError_t e)
@@ -128,6 +129,8 @@ ClassifyArgs make_args(const int32_t *points, int64_t n_points, const int32_t *p
 }
 
 }  // namespace
+
+void pipdev::note_launch(int n) { g_launches.fetch_add((unsigned long long)n); }
 
 namespace pipdev {
 Tuning current_tuning() { return Tuning{g_edge_tile.load(), g_ppt.load(), g_ctas.load()}; }
@@ -322,7 +325,9 @@ const char *pip_status_str(int code)
 
 int pip_last_cuda_error(void) { return g_last_cuda; }
 
-int pip_version(void) { return 100; }
+int pip_version(void) { return 101; }
+
+uint64_t pip_launch_count(void) { return g_launches.load(); }
 
 }  // extern "C"
 
@@ -364,6 +369,7 @@ int launch_validate(const ClassifyArgs &a, long long n_verts, long long n_cand_i
                     cudaStream_t stream)
 {
     k_validate<<<grid, 256, 0, stream>>>(a, n_verts, n_cand_ids, d_status);
+    note_launch();
     return (int)cudaGetLastError();
 }
 

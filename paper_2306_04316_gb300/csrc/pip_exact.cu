@@ -101,6 +101,7 @@ __global__ void __launch_bounds__(256) k_pip_exact(ClassifyArgs a, long long tot
 int launch_exact(const ClassifyArgs &a, long long total_bits, int grid, cudaStream_t stream)
 {
     k_pip_exact<<<grid, 256, 0, stream>>>(a, total_bits);
+    note_launch();
     return (int)cudaGetLastError();
 }
 

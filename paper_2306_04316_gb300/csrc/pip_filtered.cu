@@ -790,6 +790,7 @@ static int launch_warp_d(const ClassifyArgs &a, LargeList *ll, int lcap, int n_s
     const long long need = (nchunk + WP_THREADS / 32 - 1) / (WP_THREADS / 32);
     const int grid = (int)std::max(1LL, std::min((long long)n_sm * bps, need));
     k_pip_warp<DENSE><<<grid, WP_THREADS, smem, stream>>>(a, ll, lcap);
+    note_launch();
     return (int)cudaGetLastError();
 }
 
@@ -802,6 +803,7 @@ static int launch_large_ppt(const ClassifyArgs &a, long long total_bits, LargeLi
     int e = ensure_smem(k_pip_large<PPT>, smem, configured);
     if (e) return e;
     k_pip_large<PPT><<<grid, LG_THREADS, smem, stream>>>(a, total_bits, ll, lcap, T);
+    note_launch();
     return (int)cudaGetLastError();
 }
 

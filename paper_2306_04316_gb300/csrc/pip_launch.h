@@ -7,6 +7,9 @@
 
 namespace pipdev {
 
+// Counts kernel launches made by the library (host side; pip_launch_count reads it).
+void note_launch(int n = 1);
+
 struct ClassifyArgs;
 
 struct LargeList;

@@ -45,6 +45,7 @@ def test_status_strings(lib):
     for code in range(-7, 1):
         assert lib.pip_status_str(code).startswith(b"PIP_")
     assert lib.pip_version() >= 100
+    assert lib.pip_launch_count() >= 0
 
 
 def test_argument_checks_return_before_any_device_call(lib):
