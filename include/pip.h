@@ -71,6 +71,11 @@ typedef struct pip_stats {
     uint64_t fallback_points;  /* candidates re-tested exactly because an FP32 sign was
                                   within the forward-error bound of zero */
     uint64_t exact_candidates; /* candidates classified by pip_classify_exact */
+    uint64_t filter_errors;    /* verification mode only (pip_set_verify): straddling pairs whose
+                                  trusted fast-path decision (int32 sign, or FP32 sign outside the
+                                  error bound) differs from the exact 64/128-bit test; 0 means the
+                                  filter was sound on every pair it trusted */
+    uint64_t verified_pairs;   /* verification mode only: trusted decisions that were rechecked */
 } pip_stats;
 
 /*
@@ -187,6 +192,16 @@ int pip_validate(const int32_t *points, int64_t n_points,
                  const int32_t *poly_offsets, const int32_t *verts, int32_t n_polys,
                  int64_t n_verts, const int32_t *cand_offsets, const int32_t *cand_ids,
                  int64_t n_cand_ids, int32_t *d_status, void *stream);
+
+/*
+ * pip_set_verify -- verification mode of pip_classify (not in the paper; a test hook for the
+ * forward-error bound of the FP32 filter).  With on = 1, later pip_classify calls run copies of
+ * the kernels that also recompute, with exact 64/128-bit integers, every straddling pair whose
+ * fast-path decision they trust, and count disagreements in pip_stats.filter_errors.  The bits
+ * are the same; the kernels are slower.  on = 0 (the default) restores the normal kernels.
+ * Returns PIP_OK, or PIP_ERR_INVALID for another value.
+ */
+int pip_set_verify(int32_t on);
 
 /* Human-readable name of a PIP_* status code. */
 const char *pip_status_str(int code);

@@ -28,7 +28,9 @@ class PipStats(ctypes.Structure):
     _fields_ = [("candidates", ctypes.c_uint64),
                 ("bbox_rejects", ctypes.c_uint64),
                 ("fallback_points", ctypes.c_uint64),
-                ("exact_candidates", ctypes.c_uint64)]
+                ("exact_candidates", ctypes.c_uint64),
+                ("filter_errors", ctypes.c_uint64),
+                ("verified_pairs", ctypes.c_uint64)]
 
 
 class PipError(RuntimeError):
@@ -64,6 +66,7 @@ _SIGS = {
     "pip_last_cuda_error": ([], ctypes.c_int),
     "pip_version": ([], ctypes.c_int),
     "pip_launch_count": ([], ctypes.c_uint64),
+    "pip_set_verify": ([_I32], ctypes.c_int),
 }
 
 

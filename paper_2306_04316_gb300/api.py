@@ -15,7 +15,7 @@ import torch
 from . import _lib
 
 __all__ = ["pip_classify", "pip_classify_exact", "pip_classify_noalloc", "pip_bin_count", "pip_bin_fill", "bin_join",
-           "pip_set_tuning", "pip_get_tuning", "pip_get_stats", "pip_reset_stats", "pip_launch_count", "pip_validate",
+           "pip_set_tuning", "pip_get_tuning", "pip_get_stats", "pip_reset_stats", "pip_launch_count", "pip_set_verify", "pip_validate",
            "out_words", "to_device"]
 
 
@@ -163,6 +163,12 @@ def pip_get_stats() -> dict:
     s = _lib.PipStats()
     _lib.check("pip_get_stats", _lib.load().pip_get_stats(ctypes.byref(s)))
     return {f: int(getattr(s, f)) for f, _ in _lib.PipStats._fields_}
+
+
+def pip_set_verify(on: bool):
+    """Verification mode: every trusted fast-path decision is rechecked exactly and
+    disagreements are counted in pip_get_stats()["filter_errors"]."""
+    _lib.check("pip_set_verify", _lib.load().pip_set_verify(1 if on else 0))
 
 
 def pip_launch_count() -> int:

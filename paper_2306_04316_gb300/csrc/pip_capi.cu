@@ -29,6 +29,7 @@ std::atomic<int> g_edge_tile{2048};
 std::atomic<int> g_ctas{4};
 std::atomic<int> g_ppt{2};
 std::atomic<unsigned long long> g_launches{0};
+std::atomic<int> g_verify{0};
 thread_local int g_last_cuda = 0;
 
 int cuda_fail(cudaError_t e)
@@ -133,7 +134,7 @@ ClassifyArgs make_args(const int32_t *points, int64_t n_points, const int32_t *p
 void pipdev::note_launch(int n) { g_launches.fetch_add((unsigned long long)n); }
 
 namespace pipdev {
-Tuning current_tuning() { return Tuning{g_edge_tile.load(), g_ppt.load(), g_ctas.load()}; }
+Tuning current_tuning() { return Tuning{g_edge_tile.load(), g_ppt.load(), g_ctas.load(), g_verify.load()}; }
 }  // namespace pipdev
 
 extern "C" {
@@ -219,6 +220,15 @@ int pip_get_stats(pip_stats *out)
     out->bbox_rejects = h[ST_BBOX_REJECTS];
     out->fallback_points = h[ST_FALLBACK_POINTS];
     out->exact_candidates = h[ST_EXACT_CANDIDATES];
+    out->filter_errors = h[ST_FILTER_ERRORS];
+    out->verified_pairs = h[ST_VERIFIED];
+    return PIP_OK;
+}
+
+int pip_set_verify(int32_t on)
+{
+    if (on != 0 && on != 1) return PIP_ERR_INVALID;
+    g_verify.store(on);
     return PIP_OK;
 }
 
@@ -325,7 +335,7 @@ const char *pip_status_str(int code)
 
 int pip_last_cuda_error(void) { return g_last_cuda; }
 
-int pip_version(void) { return 101; }
+int pip_version(void) { return 102; }
 
 uint64_t pip_launch_count(void) { return g_launches.load(); }
 

@@ -23,6 +23,8 @@ enum StatIdx {
     ST_BBOX_REJECTS = 1,
     ST_FALLBACK_POINTS = 2,
     ST_EXACT_CANDIDATES = 4,
+    ST_FILTER_ERRORS = 5,     // verification mode: fast-path decisions that the exact test contradicts
+    ST_VERIFIED = 6,          // verification mode: fast-path decisions checked
     ST_COUNT = 8
 };
 

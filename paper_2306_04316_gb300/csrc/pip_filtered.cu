@@ -198,7 +198,7 @@ __device__ __forceinline__ float4 fp32_record(int2 ri, int2 rj, int ox, int oy)
     return dy > 0 ? make_float4(c, fdy, fdx, __int_as_float(rj.y)) : make_float4(-c, -fdy, -fdx, __int_as_float(rj.y));
 }
 
-template <bool DENSE>
+template <bool DENSE, bool VERIFY>
 __global__ void __launch_bounds__(WP_THREADS, WP_CTAS) k_pip_warp(ClassifyArgs a, LargeList *ll, int lcap)
 {
     using CI = typename std::conditional<DENSE, long long, int>::type;
@@ -213,7 +213,7 @@ __global__ void __launch_bounds__(WP_THREADS, WP_CTAS) k_pip_warp(ClassifyArgs a
     const int nchunk = (P + 31) >> 5;
     const int gw = blockIdx.x * (WP_THREADS / 32) + (threadIdx.x >> 5);
     const int nw = gridDim.x * (WP_THREADS / 32);
-    unsigned st_cand = 0, st_rej = 0, st_fbp = 0;
+    unsigned st_cand = 0, st_rej = 0, st_fbp = 0, st_err = 0, st_ver = 0;
     if (!DENSE && gw == 0 && lane == 0 && P > 0) {
         // bits past the last candidate in the final word are 0
         const long long C = __ldg(a.cand_offsets + P);
@@ -422,10 +422,17 @@ __global__ void __launch_bounds__(WP_THREADS, WP_CTAS) k_pip_warp(ClassifyArgs a
                         unsigned acc = 0;
                         #pragma unroll 4
                         for (int k = 0; k < ki; ++k) {
+                            const unsigned acur = ad;
                             const int4 q4 = lds128(ad);
                             ad = __viaddmin_u32(ad, 16u, al);
                             const unsigned u = py - (unsigned)q4.w;
                             const unsigned nt = (unsigned)q4.x + px * (unsigned)q4.y + py * (unsigned)q4.z;
+                            if (VERIFY && (int)(u ^ up) < 0) {   // a straddling edge: its exact test
+                                const int e = (int)((acur - rec_base) >> 4);
+                                const int2 ri = S.v[e], rj = S.v[e + 1 == e1 ? e0 : e + 1];
+                                st_err += exact_edge_counts(p2.x, p2.y, ri.x, ri.y, rj.x, rj.y) != (int)(nt >> 31);
+                                ++st_ver;
+                            }
                             acc ^= (u ^ up) & nt;
                             up = u;
                         }
@@ -445,6 +452,7 @@ __global__ void __launch_bounds__(WP_THREADS, WP_CTAS) k_pip_warp(ClassifyArgs a
                         int par = 0;
                         #pragma unroll 2
                         for (int k = 0; k < kf; ++k) {
+                            const unsigned acur = ad;
                             const int4 q4 = lds128(ad);
                             ad = __viaddmin_u32(ad, 16u, al);
                             const bool sn = q4.w > py;
@@ -452,6 +460,12 @@ __global__ void __launch_bounds__(WP_THREADS, WP_CTAS) k_pip_warp(ClassifyArgs a
                             sp = sn;
                             float tt = __fmaf_rn(-Px, __int_as_float(q4.y), __int_as_float(q4.x));
                             tt = __fmaf_rn(Py, __int_as_float(q4.z), tt);
+                            if (VERIFY && gf && st && !(fabsf(tt) <= B)) {   // a trusted FP32 sign
+                                const int e = (int)((acur - rec_base) >> 4);
+                                const int2 ri = S.v[e], rj = S.v[e + 1 == e1 ? e0 : e + 1];
+                                st_err += exact_edge_counts(p2.x, p2.y, ri.x, ri.y, rj.x, rj.y) != (int)(tt > 0.f);
+                                ++st_ver;
+                            }
                             par ^= (int)(st & (tt > 0.f));
                             unc |= st & (fabsf(tt) <= B);
                         }
@@ -487,11 +501,15 @@ __global__ void __launch_bounds__(WP_THREADS, WP_CTAS) k_pip_warp(ClassifyArgs a
             st_cand += __shfl_down_sync(FULL, st_cand, o);
             st_rej += __shfl_down_sync(FULL, st_rej, o);
             st_fbp += __shfl_down_sync(FULL, st_fbp, o);
+            if (VERIFY) st_err += __shfl_down_sync(FULL, st_err, o);
+            if (VERIFY) st_ver += __shfl_down_sync(FULL, st_ver, o);
         }
         if (lane == 0) {
+            if (VERIFY && st_ver) atomicAdd(a.stats + ST_VERIFIED, (unsigned long long)st_ver);
             if (st_cand) atomicAdd(a.stats + ST_CANDIDATES, (unsigned long long)st_cand);
             if (st_rej) atomicAdd(a.stats + ST_BBOX_REJECTS, (unsigned long long)st_rej);
             if (st_fbp) atomicAdd(a.stats + ST_FALLBACK_POINTS, (unsigned long long)st_fbp);
+            if (VERIFY && st_err) atomicAdd(a.stats + ST_FILTER_ERRORS, (unsigned long long)st_err);
         }
     }
 }
@@ -511,10 +529,11 @@ size_t filtered_smem_bytes(int T)
 // s_v[e + 1]; record e holds the edge's bound in .w): one shared record load serves every
 // candidate, and the PPT chains are independent.  Candidates whose FP32 sign came within the
 // bound of zero are redone exactly.
-template <int PPT>
+template <int PPT, bool VERIFY>
 __device__ __forceinline__ void tile_parity_multi(const float4 *__restrict__ s_rec, const int2 *__restrict__ s_v,
                                                   int nt, const int2 (&p)[PPT], const bool (&ok)[PPT], int ox,
-                                                  int oy, int (&par)[PPT], unsigned long long &n_fb_pts)
+                                                  int oy, int (&par)[PPT], unsigned long long &n_fb_pts,
+                                                  unsigned long long &n_err, unsigned long long &n_ver)
 {
     // one candidate at a time: the side of the previous vertex is carried in one predicate
     #pragma unroll 1
@@ -533,6 +552,11 @@ __device__ __forceinline__ void tile_parity_multi(const float4 *__restrict__ s_r
             sp = sn;
             float t = __fmaf_rn(-Px, q.y, q.x);
             t = __fmaf_rn(Py, q.z, t);
+            if (VERIFY && st && !(fabsf(t) <= q.w)) {   // a trusted FP32 sign: its exact test
+                const int2 ri = s_v[e], rj = s_v[e + 1];
+                n_err += exact_edge_counts(p[r].x, p[r].y, ri.x, ri.y, rj.x, rj.y) != (int)(t > 0.f);
+                ++n_ver;
+            }
             pr ^= (int)(st & (t > 0.f));
             unc += (int)(st & (fabsf(t) <= q.w));
         }
@@ -556,7 +580,7 @@ __device__ __forceinline__ int slice_edges(long long m, long long nb, int nlarge
     return (int)((es + 31) & ~31LL);
 }
 
-template <int PPT>
+template <int PPT, bool VERIFY>
 __global__ void __launch_bounds__(LG_THREADS) k_pip_large(ClassifyArgs a, long long total_bits, LargeList *ll,
                                                          int lcap, int T)
 {
@@ -572,7 +596,7 @@ __global__ void __launch_bounds__(LG_THREADS) k_pip_large(ClassifyArgs a, long l
     const bool dense = a.cand_offsets == nullptr;
     const int P = a.n_polys;
     const long long W32 = a.words_per_poly * 32;
-    unsigned long long st_cand = 0, st_fbp = 0;
+    unsigned long long st_cand = 0, st_fbp = 0, st_err = 0, st_ver = 0;
     const int count = *((volatile int *)&ll->count);
     const bool scan = *((volatile int *)&ll->overflow) != 0;
     if (count == 0 && !scan) return;   // nothing listed: the header is already clear for the next call
@@ -709,7 +733,7 @@ __global__ void __launch_bounds__(LG_THREADS) k_pip_large(ClassifyArgs a, long l
                 s_rec[i] = rec;
             }
             __syncthreads();
-            tile_parity_multi<PPT>(s_rec, s_v, nt, pt, ok, ox, oy, par, st_fbp);
+            tile_parity_multi<PPT, VERIFY>(s_rec, s_v, nt, pt, ok, ox, oy, par, st_fbp, st_err, st_ver);
             __syncthreads();
         }
         // XOR the partial parities into the output words (the block need not be word-aligned)
@@ -733,10 +757,14 @@ __global__ void __launch_bounds__(LG_THREADS) k_pip_large(ClassifyArgs a, long l
         for (int o = 16; o > 0; o >>= 1) {
             st_cand += __shfl_down_sync(FULL, st_cand, o);
             st_fbp += __shfl_down_sync(FULL, st_fbp, o);
+            if (VERIFY) st_err += __shfl_down_sync(FULL, st_err, o);
+            if (VERIFY) st_ver += __shfl_down_sync(FULL, st_ver, o);
         }
         if (lane == 0) {
             if (st_cand) atomicAdd(a.stats + ST_CANDIDATES, st_cand);
             if (st_fbp) atomicAdd(a.stats + ST_FALLBACK_POINTS, st_fbp);
+            if (VERIFY && st_err) atomicAdd(a.stats + ST_FILTER_ERRORS, st_err);
+            if (VERIFY && st_ver) atomicAdd(a.stats + ST_VERIFIED, st_ver);
         }
     }
     // the last CTA to finish empties the list for the next call
@@ -769,19 +797,20 @@ static int ensure_smem(K kernel, size_t smem, size_t *configured)
     return 0;
 }
 
-template <bool DENSE>
+template <bool DENSE, bool VERIFY>
 static int launch_warp_d(const ClassifyArgs &a, LargeList *ll, int lcap, int n_sm, cudaStream_t stream)
 {
     static size_t configured[64] = {0};
     static int blocks_per_sm[64] = {0};
     const size_t smem = sizeof(WarpSmem) * (WP_THREADS / 32);
-    int e = ensure_smem(k_pip_warp<DENSE>, smem, configured);
+    int e = ensure_smem(k_pip_warp<DENSE, VERIFY>, smem, configured);
     if (e) return e;
     int dev = 0;
     cudaGetDevice(&dev);
     if (dev >= 0 && dev < 64 && blocks_per_sm[dev] == 0) {
         int nb = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_pip_warp<DENSE>, WP_THREADS, smem) != cudaSuccess)
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_pip_warp<DENSE, VERIFY>, WP_THREADS, smem) !=
+            cudaSuccess)
             nb = 1;
         blocks_per_sm[dev] = std::max(nb, 1);
     }
@@ -789,36 +818,44 @@ static int launch_warp_d(const ClassifyArgs &a, LargeList *ll, int lcap, int n_s
     const long long nchunk = ((long long)a.n_polys + 31) / 32;
     const long long need = (nchunk + WP_THREADS / 32 - 1) / (WP_THREADS / 32);
     const int grid = (int)std::max(1LL, std::min((long long)n_sm * bps, need));
-    k_pip_warp<DENSE><<<grid, WP_THREADS, smem, stream>>>(a, ll, lcap);
+    k_pip_warp<DENSE, VERIFY><<<grid, WP_THREADS, smem, stream>>>(a, ll, lcap);
     note_launch();
     return (int)cudaGetLastError();
 }
 
-template <int PPT>
+template <int PPT, bool VERIFY>
 static int launch_large_ppt(const ClassifyArgs &a, long long total_bits, LargeList *ll, int lcap, int T, int grid,
                             cudaStream_t stream)
 {
     static size_t configured[64] = {0};
     const size_t smem = filtered_smem_bytes(T);
-    int e = ensure_smem(k_pip_large<PPT>, smem, configured);
+    int e = ensure_smem(k_pip_large<PPT, VERIFY>, smem, configured);
     if (e) return e;
-    k_pip_large<PPT><<<grid, LG_THREADS, smem, stream>>>(a, total_bits, ll, lcap, T);
+    k_pip_large<PPT, VERIFY><<<grid, LG_THREADS, smem, stream>>>(a, total_bits, ll, lcap, T);
     note_launch();
     return (int)cudaGetLastError();
+}
+
+template <bool VERIFY>
+static int launch_filtered_v(const ClassifyArgs &a, long long total_bits, const Tuning &t, int n_sm, LargeList *ll,
+                             int lcap, cudaStream_t stream)
+{
+    int e = a.cand_offsets ? launch_warp_d<false, VERIFY>(a, ll, lcap, n_sm, stream)
+                           : launch_warp_d<true, VERIFY>(a, ll, lcap, n_sm, stream);
+    if (e) return e;
+    const int grid = n_sm * t.ctas_per_sm;
+    switch (t.pts_per_thread) {
+        case 1: return launch_large_ppt<1, VERIFY>(a, total_bits, ll, lcap, t.edge_tile, grid, stream);
+        case 4: return launch_large_ppt<4, VERIFY>(a, total_bits, ll, lcap, t.edge_tile, grid, stream);
+        default: return launch_large_ppt<2, VERIFY>(a, total_bits, ll, lcap, t.edge_tile, grid, stream);
+    }
 }
 
 int launch_filtered(const ClassifyArgs &a, long long total_bits, const Tuning &t, int n_sm, LargeList *ll, int lcap,
                     cudaStream_t stream)
 {
-    int e = a.cand_offsets ? launch_warp_d<false>(a, ll, lcap, n_sm, stream)
-                           : launch_warp_d<true>(a, ll, lcap, n_sm, stream);
-    if (e) return e;
-    const int grid = n_sm * t.ctas_per_sm;
-    switch (t.pts_per_thread) {
-        case 1: return launch_large_ppt<1>(a, total_bits, ll, lcap, t.edge_tile, grid, stream);
-        case 4: return launch_large_ppt<4>(a, total_bits, ll, lcap, t.edge_tile, grid, stream);
-        default: return launch_large_ppt<2>(a, total_bits, ll, lcap, t.edge_tile, grid, stream);
-    }
+    return t.verify ? launch_filtered_v<true>(a, total_bits, t, n_sm, ll, lcap, stream)
+                    : launch_filtered_v<false>(a, total_bits, t, n_sm, ll, lcap, stream);
 }
 
 }  // namespace pipdev

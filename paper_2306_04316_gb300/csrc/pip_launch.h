@@ -19,6 +19,7 @@ struct Tuning {
     int edge_tile;       // edges staged in shared memory per pass
     int pts_per_thread;  // candidates carried by each thread (1, 2, 4)
     int ctas_per_sm;     // resident CTAs per SM
+    int verify;          // recheck every trusted decision exactly and count disagreements
 };
 
 int launch_exact(const ClassifyArgs &a, long long total_bits, int grid, cudaStream_t stream);

@@ -323,3 +323,36 @@ def test_full_range_boxes_points_on_extremes(api):
     ids = list(range(len(pts)))
     check_full(api, make("full-range-csr", polys, pts, [ids] * len(polys)))
     check_full(api, make("full-range-dense", polys, pts))
+
+
+# ------------------------------------------------------------------------------------------
+# soundness of the fast paths (verification mode)
+# ------------------------------------------------------------------------------------------
+
+def _verify_cases():
+    return [
+        ("footprints", lambda: W.footprints(seed=9, n_polys=20_000)),          # int32 path
+        ("stress", lambda: W.stress(seed=10, n_polys=40_000)),                 # FP32 filter, full range
+        ("star", lambda: W.star()),                                           # large-polygon kernel
+        ("fractal", lambda: W.fractal(seed=11, n_polys=4, m_lo=3_000, m_hi=20_000, n_points=60_000,
+                                      cell=300_000, grid=2)),
+    ]
+
+
+@pytest.mark.parametrize("name,make_w", _verify_cases(), ids=[c[0] for c in _verify_cases()])
+def test_verification_mode_finds_no_unsound_decision(api, name, make_w):
+    """Every straddling pair whose fast-path decision the kernels trust (the int32 sign, or an
+    FP32 sign outside the forward-error bound) is recomputed exactly: no disagreement, and the
+    bits still equal the oracle's."""
+    w = make_w()
+    want = oracle.classify(w.points, w.poly_offsets, w.verts, w.cand_offsets, w.cand_ids)
+    api.pip_set_verify(True)
+    try:
+        api.pip_reset_stats()
+        got = gpu_bits(api, w)
+        s = api.pip_get_stats()
+    finally:
+        api.pip_set_verify(False)
+    assert_same(got, want, w.n_bits, f"{name} (verification mode)")
+    assert s["verified_pairs"] > 0
+    assert s["filter_errors"] == 0, f"{s['filter_errors']} of {s['verified_pairs']} trusted decisions were wrong"
