@@ -399,6 +399,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="footprints", choices=["footprints", "stress", "star", "fractal", "join"])
     ap.add_argument("--kernel", default="filtered", choices=["filtered", "exact"])
+    ap.add_argument("--semantics", default="halfopen", choices=["halfopen", "alg1", "alg2"],
+                    help="alg1/alg2: time the paper's printed Algorithm 1 or 2 (pip_classify_paper) and "
+                         "count the bits where it differs from the half-open rule")
     ap.add_argument("--scale", type=float, default=1.0, help="fraction of the full batch (tests only)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -433,6 +436,11 @@ def main():
     n_words = w.n_words
     out = torch.empty(n_words, dtype=torch.int32, device="cuda")
     fn = api.pip_classify if args.kernel == "filtered" else api.pip_classify_exact
+    if args.semantics != "halfopen":
+        algorithm = 1 if args.semantics == "alg1" else 2
+
+        def fn(*a_, **k_):
+            return api.pip_classify_paper(*a_, algorithm=algorithm, **k_)
     cand_o, cand_i = d.get("cand_offsets"), d.get("cand_ids")
 
     def step():
@@ -542,6 +550,15 @@ def main():
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = oracle_baseline(w)
+    semantics = None
+    if args.semantics != "halfopen":
+        # bits where the paper's printed rule and the half-open rule disagree (not timed)
+        ref = api.pip_classify(d["points"], d["poly_offsets"], d["verts"], cand_o, cand_i)
+        fn(d["points"], d["poly_offsets"], d["verts"], cand_o, cand_i, out=out)
+        x = torch.bitwise_xor(out[:n_words], ref[:n_words]).view(torch.uint8).cpu().numpy()
+        diff = int(np.unpackbits(x).sum())
+        semantics = {"rule": args.semantics, "bits_differing_from_half_open": diff,
+                     "fraction_of_candidates": diff / max(1, w.n_candidates)}
 
     if rank == 0:
         stats = api.pip_get_stats()
@@ -565,6 +582,11 @@ def main():
                              "value": (T / (other_ms / 1000.0)) if other_ms else None},
             "fallback_fraction": (stats["fallback_points"] / stats["candidates"]) if stats["candidates"] else None,
         }
+        if semantics:
+            line["semantics"] = semantics
+            line["config"]["kernel"] = f"paper {args.semantics} (plain exact kernel)"
+            line["roofline"]["kernel"] = "k_pip_exact (paper rule)"
+            line["dtype"] = "i64" if args.semantics == "alg1" else "f64"
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()

@@ -108,6 +108,27 @@ int pip_classify_exact(const int32_t *points, int64_t n_points,
                        uint32_t *out_bits, void *stream);
 
 /*
+ * pip_classify_paper -- the paper's printed algorithms, evaluated literally, to measure how
+ * often their rule for points on the ray or on the boundary differs from the half-open rule of
+ * pip_classify (same arguments and output layout, plus `algorithm`):
+ *   1  Algorithm 1 (Constraint 1): an edge R_i -> R_{i+1} is a candidate when
+ *      f_i f_{i+1} <= 0 with f = y - p_y (horizontal edges on the ray included), the normal
+ *      n = (d_y, -d_x) is flipped when n_x < 0, and the edge counts when (p - R_i) . n <= 0;
+ *      exact integers.
+ *   2  Algorithm 2 (Constraint 2): the same candidates; the edge counts when
+ *      x_i + ((p_y - y_i) / d_y) d_x > p_x, evaluated in IEEE float64 with one rounding per
+ *      operation (0/0 gives NaN, which never counts).
+ * The polygon is R_0 .. R_{m-1} with R_m = R_0 (the paper's convention), as in pip_classify.
+ * Both rules agree with pip_classify at points whose y differs from every vertex's y and that
+ * lie on no edge; they differ on the boundary and on rays through vertices or along edges.
+ * Plain exact kernel; returns PIP_OK, PIP_ERR_INVALID for another `algorithm`, or PIP_ERR_*.
+ */
+int pip_classify_paper(const int32_t *points, int64_t n_points,
+                       const int32_t *poly_offsets, const int32_t *verts, int32_t n_polys,
+                       const int32_t *cand_offsets, const int32_t *cand_ids, int32_t algorithm,
+                       uint32_t *out_bits, void *stream);
+
+/*
  * pip_classify_noalloc -- pip_classify for callers that cannot allocate device memory (the
  * paper has no counterpart).  pip_classify allocates, on its first call on each stream, the
  * device list that hands large polygons to its second kernel (and, once per device, its

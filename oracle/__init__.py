@@ -29,8 +29,8 @@ def build(force: bool = False) -> str:
     """Compile ``oracle.c`` into ``liboracle.so`` (plain gcc, -O2, pthreads)."""
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         tmp = _LIB + ".tmp%d" % os.getpid()
-        subprocess.check_call(["gcc", "-O2", "-std=gnu11", "-shared", "-fPIC", "-pthread",
-                               "-o", tmp, _SRC])
+        subprocess.check_call(["gcc", "-O2", "-std=gnu11", "-ffp-contract=off", "-shared", "-fPIC",
+                               "-pthread", "-o", tmp, _SRC])
         os.replace(tmp, _LIB)
     return _LIB
 
@@ -42,6 +42,9 @@ def open_library(path: str):
     lib.oracle_classify.argtypes = [P, ctypes.c_int64, P, P, ctypes.c_int32, P, P, P,
                                     ctypes.c_int]
     lib.oracle_classify.restype = ctypes.c_int
+    lib.oracle_classify_rule.argtypes = [P, ctypes.c_int64, P, P, ctypes.c_int32, P, P, ctypes.c_int, P,
+                                         ctypes.c_int]
+    lib.oracle_classify_rule.restype = ctypes.c_int
     lib.oracle_classify_sample.argtypes = [P, ctypes.c_int64, P, P, ctypes.c_int32, P, P,
                                            P, ctypes.c_int64, P]
     lib.oracle_classify_sample.restype = ctypes.c_int
@@ -108,6 +111,26 @@ def classify(points, poly_offsets, verts, cand_offsets=None, cand_ids=None, thre
                              int(threads or default_threads()))
     if rc != 0:
         raise ValueError("oracle_classify rejected its arguments")
+    return out
+
+
+def classify_rule(points, poly_offsets, verts, rule, cand_offsets=None, cand_ids=None, threads=None):
+    """Like ``classify`` with the paper's printed rule: 1 = Algorithm 1, 2 = Algorithm 2
+    (0 = the half-open rule of ``classify``)."""
+    lib = _load()
+    points = _i32(points, (2,))
+    verts = _i32(verts, (2,))
+    poly_offsets = _i32(poly_offsets)
+    n_polys = len(poly_offsets) - 1
+    if cand_offsets is not None:
+        cand_offsets = _i32(cand_offsets)
+        cand_ids = _i32(cand_ids)
+    out = np.zeros(n_out_words(len(points), n_polys, cand_offsets), dtype=np.uint32)
+    rc = lib.oracle_classify_rule(_ptr(points), len(points), _ptr(poly_offsets), _ptr(verts), n_polys,
+                                  _ptr(cand_offsets), _ptr(cand_ids), int(rule), _ptr(out),
+                                  int(threads or default_threads()))
+    if rc != 0:
+        raise ValueError("oracle_classify_rule rejected its arguments")
     return out
 
 

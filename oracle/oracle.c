@@ -30,6 +30,18 @@
  * line_pos in 128-bit integers, so no step rounds or overflows for any int32
  * input.  Work is split over points with POSIX threads (the paper parallelises
  * over points with Numba prange, Algorithm 4).
+ *
+ * oracle_classify_rule also evaluates the paper's printed algorithms literally,
+ * to measure how often their rule differs from the one above:
+ *   rule 1 (Algorithm 1, Constraint 1): an edge is a candidate when
+ *          f_i * f_{i+1} <= 0 (both vertices on or across the ray, horizontal
+ *          edges on the ray included), n = (d_y, -d_x) flipped when n_x < 0,
+ *          and it counts when (p - r_i) . n <= 0 -- exact integers;
+ *   rule 2 (Algorithm 2, Constraint 2): the same candidates, the crossing
+ *          abscissa x_new = x_i + ((p_y - y_i) / d_y) d_x in IEEE float64 (a
+ *          division 0/0 gives NaN), and it counts when x_new > p_x.  The
+ *          float64 operations are the three the algorithm writes, each rounded
+ *          once (the file is compiled without floating-point contraction).
  */
 #include <stdint.h>
 #include <stdlib.h>
@@ -60,6 +72,49 @@ static int oracle_point_in_polygon(int64_t px, int64_t py, const int32_t *v, int
     return (int)(count & 1);                    /* step 7 */
 }
 
+/* Algorithm 1 as printed (Constraint 1, inclusive tests). */
+static int paper_alg1(int64_t px, int64_t py, const int32_t *v, int64_t m)
+{
+    int64_t counted = 0;
+    for (int64_t e = 0; e < m; ++e) {
+        const int32_t *r = v + 2 * e, *s = v + 2 * ((e + 1 < m) ? e + 1 : 0);
+        int64_t fa = (int64_t)r[1] - py, fb = (int64_t)s[1] - py;
+        if ((i128)fa * fb > 0)                  /* not a candidate */
+            continue;
+        int64_t nx = (int64_t)s[1] - r[1], ny = (int64_t)r[0] - s[0];
+        if (nx < 0) { nx = -nx; ny = -ny; }
+        i128 lp = (i128)(px - r[0]) * nx + (i128)(py - r[1]) * ny;
+        if (lp <= 0)
+            ++counted;
+    }
+    return (int)(counted & 1);
+}
+
+/* Algorithm 2 as printed (Constraint 2, float64 crossing abscissa). */
+static int paper_alg2(int64_t px, int64_t py, const int32_t *v, int64_t m)
+{
+    int64_t counted = 0;
+    for (int64_t e = 0; e < m; ++e) {
+        const int32_t *r = v + 2 * e, *s = v + 2 * ((e + 1 < m) ? e + 1 : 0);
+        int64_t fa = (int64_t)r[1] - py, fb = (int64_t)s[1] - py;
+        if ((i128)fa * fb > 0)
+            continue;
+        double dxe = (double)((int64_t)s[0] - r[0]), dye = (double)((int64_t)s[1] - r[1]);
+        double lam = (double)(py - r[1]) / dye;      /* NaN when 0 / 0 */
+        double x_new = (double)r[0] + lam * dxe;
+        if (x_new > (double)px)
+            ++counted;
+    }
+    return (int)(counted & 1);
+}
+
+static int classify_point(int rule, int64_t px, int64_t py, const int32_t *v, int64_t m)
+{
+    if (rule == 1) return paper_alg1(px, py, v, m);
+    if (rule == 2) return paper_alg2(px, py, v, m);
+    return oracle_point_in_polygon(px, py, v, m);
+}
+
 int oracle_pip_single(int32_t px, int32_t py, const int32_t *verts, int64_t m)
 {
     if (m < 0 || (m > 0 && !verts)) return -1;
@@ -79,6 +134,7 @@ typedef struct {
     int64_t n_bits;          /* candidates (CSR) or n_polys * 32 * W (dense) */
     int64_t words_per_poly;  /* dense only: W = ceil(n_points / 32) */
     int64_t word_lo, word_hi;
+    int rule;                /* 0 half-open (the method), 1 Algorithm 1, 2 Algorithm 2 */
 } job_t;
 
 /* Largest k with cand_offsets[k] <= c (the polygon owning candidate c). */
@@ -112,8 +168,8 @@ static void *run_words(void *arg)
                 if (pid >= J->n_points) continue;
             }
             int64_t v0 = J->poly_offsets[k], v1 = J->poly_offsets[k + 1];
-            int bit = oracle_point_in_polygon(J->points[2 * pid], J->points[2 * pid + 1],
-                                              J->verts + 2 * v0, v1 - v0);
+            int bit = classify_point(J->rule, J->points[2 * pid], J->points[2 * pid + 1],
+                                     J->verts + 2 * v0, v1 - v0);
             word |= (uint32_t)bit << b;
         }
         J->out_bits[w] = word;
@@ -133,12 +189,12 @@ static void *run_words(void *arg)
  *   n_threads    <= 0 means one thread.
  * Returns 0, or -1 on a NULL or size error.
  */
-int oracle_classify(const int32_t *points, int64_t n_points,
-                    const int32_t *poly_offsets, const int32_t *verts, int32_t n_polys,
-                    const int32_t *cand_offsets, const int32_t *cand_ids,
-                    uint32_t *out_bits, int n_threads)
+int oracle_classify_rule(const int32_t *points, int64_t n_points,
+                         const int32_t *poly_offsets, const int32_t *verts, int32_t n_polys,
+                         const int32_t *cand_offsets, const int32_t *cand_ids,
+                         int rule, uint32_t *out_bits, int n_threads)
 {
-    if (n_points < 0 || n_polys < 0) return -1;
+    if (n_points < 0 || n_polys < 0 || rule < 0 || rule > 2) return -1;
     if ((cand_offsets == NULL) != (cand_ids == NULL)) return -1;
     if (n_polys > 0 && !poly_offsets) return -1;
     job_t base;
@@ -146,6 +202,7 @@ int oracle_classify(const int32_t *points, int64_t n_points,
     base.points = points; base.n_points = n_points;
     base.poly_offsets = poly_offsets; base.verts = verts; base.n_polys = n_polys;
     base.cand_offsets = cand_offsets; base.cand_ids = cand_ids; base.out_bits = out_bits;
+    base.rule = rule;
     if (cand_offsets) {
         base.n_bits = n_polys > 0 ? cand_offsets[n_polys] : 0;
     } else {
@@ -171,6 +228,15 @@ int oracle_classify(const int32_t *points, int64_t n_points,
     for (int t = 1; t < n_threads; ++t)
         pthread_join(tid[t], NULL);
     return 0;
+}
+
+int oracle_classify(const int32_t *points, int64_t n_points,
+                    const int32_t *poly_offsets, const int32_t *verts, int32_t n_polys,
+                    const int32_t *cand_offsets, const int32_t *cand_ids,
+                    uint32_t *out_bits, int n_threads)
+{
+    return oracle_classify_rule(points, n_points, poly_offsets, verts, n_polys, cand_offsets,
+                                cand_ids, 0, out_bits, n_threads);
 }
 
 /*

@@ -14,7 +14,7 @@ import torch
 
 from . import _lib
 
-__all__ = ["pip_classify", "pip_classify_exact", "pip_classify_noalloc", "pip_bin_count", "pip_bin_fill", "bin_join",
+__all__ = ["pip_classify", "pip_classify_exact", "pip_classify_paper", "pip_classify_noalloc", "pip_bin_count", "pip_bin_fill", "bin_join",
            "pip_set_tuning", "pip_get_tuning", "pip_get_stats", "pip_reset_stats", "pip_launch_count", "pip_set_verify", "pip_validate",
            "out_words", "to_device"]
 
@@ -56,7 +56,7 @@ def to_device(workload, device="cuda"):
     return d
 
 
-def _classify(fn_name, points, poly_offsets, verts, cand_offsets, cand_ids, out, n_cands, stream):
+def _classify(fn_name, points, poly_offsets, verts, cand_offsets, cand_ids, out, n_cands, stream, extra=()):
     lib = _lib.load()
     _need(points, "points", 2)
     _need(poly_offsets, "poly_offsets")
@@ -72,7 +72,7 @@ def _classify(fn_name, points, poly_offsets, verts, cand_offsets, cand_ids, out,
         out = torch.empty(max(nw, 1), dtype=torch.int32, device=points.device)
     _need(out, "out")
     rc = getattr(lib, fn_name)(_ptr(points), n_points, _ptr(poly_offsets), _ptr(verts), n_polys,
-                               _ptr(cand_offsets), _ptr(cand_ids), _ptr(out), _stream(stream))
+                               _ptr(cand_offsets), _ptr(cand_ids), *extra, _ptr(out), _stream(stream))
     _lib.check(fn_name, rc)
     return out
 
@@ -89,6 +89,13 @@ def pip_classify_exact(points, poly_offsets, verts, cand_offsets=None, cand_ids=
     """Plain exact integer classification (``pip_classify_exact``); returns out_bits."""
     return _classify("pip_classify_exact", points, poly_offsets, verts, cand_offsets, cand_ids,
                      out, n_cands, stream)
+
+
+def pip_classify_paper(points, poly_offsets, verts, cand_offsets=None, cand_ids=None, algorithm=1,
+                       out=None, n_cands=None, stream=None):
+    """The paper's Algorithm 1 or 2 evaluated literally (``pip_classify_paper``)."""
+    return _classify("pip_classify_paper", points, poly_offsets, verts, cand_offsets, cand_ids, out,
+                     n_cands, stream, extra=(int(algorithm),))
 
 
 def pip_classify_noalloc(points, poly_offsets, verts, cand_offsets=None, cand_ids=None, out=None,

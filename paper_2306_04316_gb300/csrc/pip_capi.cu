@@ -163,9 +163,12 @@ int pip_classify(const int32_t *points, int64_t n_points, const int32_t *poly_of
     return e == 0 ? PIP_OK : cuda_fail((cudaError_t)e);
 }
 
-int pip_classify_exact(const int32_t *points, int64_t n_points, const int32_t *poly_offsets,
-                       const int32_t *verts, int32_t n_polys, const int32_t *cand_offsets,
-                       const int32_t *cand_ids, uint32_t *out_bits, void *stream)
+}  // extern "C"
+
+namespace {
+int classify_exact_rule(const int32_t *points, int64_t n_points, const int32_t *poly_offsets,
+                        const int32_t *verts, int32_t n_polys, const int32_t *cand_offsets,
+                        const int32_t *cand_ids, uint32_t *out_bits, void *stream, int rule)
 {
     int rc = check_classify(points, n_points, poly_offsets, verts, n_polys, cand_offsets, cand_ids, out_bits);
     if (rc != PIP_OK) return rc;
@@ -178,12 +181,32 @@ int pip_classify_exact(const int32_t *points, int64_t n_points, const int32_t *p
     rc = device_state(s, &ds);
     if (rc != PIP_OK) return rc;
     ClassifyArgs a = make_args(points, n_points, poly_offsets, verts, n_polys, cand_offsets, cand_ids,
-                               out_bits, ds->stats);
+                               out_bits, rule == 0 ? ds->stats : nullptr);
     long long grid = (long long)ds->n_sm * 8;
     if (dense) grid = std::min(grid, (total_bits / 32 + 7) / 8);
     if (grid < 1) grid = 1;
-    int e = launch_exact(a, total_bits, (int)grid, s);
+    int e = launch_exact(a, total_bits, (int)grid, s, rule);
     return e == 0 ? PIP_OK : cuda_fail((cudaError_t)e);
+}
+}  // namespace
+
+extern "C" {
+
+int pip_classify_exact(const int32_t *points, int64_t n_points, const int32_t *poly_offsets,
+                       const int32_t *verts, int32_t n_polys, const int32_t *cand_offsets,
+                       const int32_t *cand_ids, uint32_t *out_bits, void *stream)
+{
+    return classify_exact_rule(points, n_points, poly_offsets, verts, n_polys, cand_offsets, cand_ids,
+                               out_bits, stream, 0);
+}
+
+int pip_classify_paper(const int32_t *points, int64_t n_points, const int32_t *poly_offsets,
+                       const int32_t *verts, int32_t n_polys, const int32_t *cand_offsets,
+                       const int32_t *cand_ids, int32_t algorithm, uint32_t *out_bits, void *stream)
+{
+    if (algorithm != 1 && algorithm != 2) return PIP_ERR_INVALID;
+    return classify_exact_rule(points, n_points, poly_offsets, verts, n_polys, cand_offsets, cand_ids,
+                               out_bits, stream, algorithm);
 }
 
 int pip_set_tuning(int32_t edge_tile, int32_t pts_per_thread, int32_t ctas_per_sm)

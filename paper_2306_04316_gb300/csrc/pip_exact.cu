@@ -6,11 +6,38 @@
 // side of the edge with int64 products (128-bit when a difference reaches 2^31), and the
 // warp packs the 32 parities with a ballot.  No staging, no local frame, no filter: this
 // is the baseline formulation the FP32-filtered kernel is measured against.
+//
+// The same kernel also evaluates the paper's printed algorithms literally (RULE 1, 2; see
+// pip_classify_paper): an edge is a candidate when f_i f_{i+1} <= 0, and it counts when
+// (p - r_i) . n <= 0 (Algorithm 1, exact integers) or when the float64 crossing abscissa
+// x_i + ((p_y - y_i) / d_y) d_x exceeds p_x (Algorithm 2, each of its three operations rounded
+// once, as IEEE float64 does; 0/0 gives NaN, which never counts).
 #include "pip_device.cuh"
 #include "pip_launch.h"
 
 namespace pipdev {
 
+// Algorithm 1's decision for a candidate edge: (p - r_i) . n <= 0, n = (d_y, -d_x) with
+// n_x >= 0.  int64 products when every difference is below 2^31, else 128-bit.
+__device__ __forceinline__ int alg1_counts(int px, int py, int xi, int yi, int xj, int yj)
+{
+    long long nx = (long long)yj - yi, ny = (long long)xi - xj;
+    if (nx < 0) { nx = -nx; ny = -ny; }
+    const long long ax = (long long)px - xi, ay = (long long)py - yi;
+    if (fits31(ax) & fits31(ay) & fits31(nx) & fits31(ny)) return ax * nx + ay * ny <= 0;
+    return (__int128)ax * nx + (__int128)ay * ny <= 0;
+}
+
+// Algorithm 2's decision for a candidate edge, in float64 with one rounding per operation.
+__device__ __forceinline__ int alg2_counts(int px, int py, int xi, int yi, int xj, int yj)
+{
+    const double dx = (double)((long long)xj - xi), dy = (double)((long long)yj - yi);
+    const double l = __ddiv_rn((double)((long long)py - yi), dy);
+    const double xn = __dadd_rn((double)xi, __dmul_rn(l, dx));
+    return xn > (double)px;
+}
+
+template <int RULE>
 __global__ void __launch_bounds__(256) k_pip_exact(ClassifyArgs a, long long total_bits)
 {
     const int lane = threadIdx.x & 31;
@@ -75,7 +102,7 @@ __global__ void __launch_bounds__(256) k_pip_exact(ClassifyArgs a, long long tot
             const int2 p = __ldg(a.points + pid);
             const int v0 = __ldg(a.poly_offsets + k), v1 = __ldg(a.poly_offsets + k + 1);
             const int m = v1 - v0;
-            if (m > 0) {
+            if (m > 0 && RULE == 0) {
                 int2 r_i = __ldg(a.verts + v1 - 1);   // closing edge first: R_{m-1} -> R_0
                 bool s_i = r_i.y > p.y;
                 for (int i = 0; i < m; ++i) {
@@ -84,6 +111,18 @@ __global__ void __launch_bounds__(256) k_pip_exact(ClassifyArgs a, long long tot
                     if (s_i != s_j) inside ^= exact_edge_counts(p.x, p.y, r_i.x, r_i.y, r_j.x, r_j.y);
                     r_i = r_j;
                     s_i = s_j;
+                }
+            } else if (m > 0) {
+                int2 r_i = __ldg(a.verts + v1 - 1);
+                int g_i = (r_i.y > p.y) - (r_i.y < p.y);   // sign of f_i
+                for (int i = 0; i < m; ++i) {
+                    const int2 r_j = __ldg(a.verts + v0 + i);
+                    const int g_j = (r_j.y > p.y) - (r_j.y < p.y);
+                    if (g_i * g_j <= 0)                      // f_i f_{i+1} <= 0
+                        inside ^= RULE == 1 ? alg1_counts(p.x, p.y, r_i.x, r_i.y, r_j.x, r_j.y)
+                                            : alg2_counts(p.x, p.y, r_i.x, r_i.y, r_j.x, r_j.y);
+                    r_i = r_j;
+                    g_i = g_j;
                 }
             }
             ++n_done;
@@ -98,9 +137,11 @@ __global__ void __launch_bounds__(256) k_pip_exact(ClassifyArgs a, long long tot
     }
 }
 
-int launch_exact(const ClassifyArgs &a, long long total_bits, int grid, cudaStream_t stream)
+int launch_exact(const ClassifyArgs &a, long long total_bits, int grid, cudaStream_t stream, int rule)
 {
-    k_pip_exact<<<grid, 256, 0, stream>>>(a, total_bits);
+    if (rule == 1) k_pip_exact<1><<<grid, 256, 0, stream>>>(a, total_bits);
+    else if (rule == 2) k_pip_exact<2><<<grid, 256, 0, stream>>>(a, total_bits);
+    else k_pip_exact<0><<<grid, 256, 0, stream>>>(a, total_bits);
     note_launch();
     return (int)cudaGetLastError();
 }

@@ -22,7 +22,7 @@ struct Tuning {
     int verify;          // recheck every trusted decision exactly and count disagreements
 };
 
-int launch_exact(const ClassifyArgs &a, long long total_bits, int grid, cudaStream_t stream);
+int launch_exact(const ClassifyArgs &a, long long total_bits, int grid, cudaStream_t stream, int rule = 0);
 int launch_filtered(const ClassifyArgs &a, long long total_bits, const Tuning &t, int n_sm, LargeList *ll,
                     int lcap, cudaStream_t stream);
 size_t filtered_smem_bytes(int edge_tile);

@@ -356,3 +356,20 @@ def test_verification_mode_finds_no_unsound_decision(api, name, make_w):
     assert_same(got, want, w.n_bits, f"{name} (verification mode)")
     assert s["verified_pairs"] > 0
     assert s["filter_errors"] == 0, f"{s['filter_errors']} of {s['verified_pairs']} trusted decisions were wrong"
+
+
+# ------------------------------------------------------------------------------------------
+# the paper's printed rules (pip_classify_paper)
+# ------------------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("algorithm", [1, 2])
+def test_paper_rules_match_the_oracle(api, algorithm):
+    for w in (W.star(), W.stress(seed=12, n_polys=30_000)):
+        d = api.to_device(w)
+        out = api.pip_classify_paper(d["points"], d["poly_offsets"], d["verts"], d.get("cand_offsets"),
+                                     d.get("cand_ids"), algorithm=algorithm,
+                                     n_cands=None if w.dense else w.n_bits)
+        torch.cuda.synchronize()
+        got = out.cpu().numpy().view(np.uint32)[:w.n_words]
+        want = oracle.classify_rule(w.points, w.poly_offsets, w.verts, algorithm, w.cand_offsets, w.cand_ids)
+        assert_same(got, want, w.n_bits, f"{w.name} algorithm {algorithm}")

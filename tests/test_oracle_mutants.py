@@ -40,7 +40,7 @@ def test_mutant_is_caught(tmp_path, name):
     c = tmp_path / "mutant.c"
     so = tmp_path / "libmutant.so"
     c.write_text(mut)
-    subprocess.check_call(["gcc", "-O1", "-std=gnu11", "-shared", "-fPIC", "-pthread",
+    subprocess.check_call(["gcc", "-O1", "-std=gnu11", "-ffp-contract=off", "-shared", "-fPIC", "-pthread",
                            "-o", str(so), str(c)])
     lib = oracle.open_library(str(so))
     caught = []
