@@ -163,13 +163,25 @@ def oracle_baseline(w, target_s=10.0, max_reps=20, max_pairs=2e10):
                 "sample": f"whole {w.name} batch ({w.n_polys} polygons, {w.n_candidates} candidates, "
                           f"{T} pair tests) x {reps} runs, {t_total:.1f} s",
                 "points_per_s": w.n_candidates * reps / t_total}
-    # sampled: candidates drawn uniformly, classified one by one (threaded over the sample)
+    # sampled: candidates drawn uniformly, classified one by one (threaded over the sample);
+    # a short probe sizes the sample to about target_s of CPU work
     rng = np.random.default_rng(12345)
     m = np.diff(w.poly_offsets.astype(np.int64))
-    owner = np.repeat(np.arange(w.n_polys), np.diff(w.cand_offsets.astype(np.int64)))
-    n = max(64, int(len(owner) * max_pairs / 20 / T))
-    sample = np.sort(rng.choice(len(owner), size=min(n, len(owner)), replace=False))
-    pairs = int(m[owner[sample]].sum())
+    owner = None if w.dense else np.repeat(np.arange(w.n_polys), np.diff(w.cand_offsets.astype(np.int64)))
+
+    def draw(n):
+        if w.dense:
+            W32 = 32 * ((w.n_points + 31) // 32)
+            s_ = np.unique(rng.integers(0, w.n_polys, n) * W32 + rng.integers(0, w.n_points, n))
+            return s_, int(m[s_ // W32].sum())
+        s_ = np.sort(rng.choice(len(owner), size=min(n, len(owner)), replace=False))
+        return s_, int(m[owner[s_]].sum())
+
+    probe, probe_pairs = draw(max(64, int(w.n_candidates * 1e8 / T)))
+    t0 = time.perf_counter()
+    _threaded_sample(w, probe, threads)
+    rate = probe_pairs / max(1e-9, time.perf_counter() - t0)
+    sample, pairs = draw(max(64, int(len(probe) * rate * target_s / max(1, probe_pairs))))
     t0 = time.perf_counter()
     _threaded_sample(w, sample, threads)
     dt = time.perf_counter() - t0
@@ -231,6 +243,8 @@ def make_workload(name, rank, scale):
         return W.star(seed=W.BASE_SEED + 1 + 1000 * rank)
     if name == "fractal":
         return W.fractal(seed=W.BASE_SEED + 4 + 1000 * rank, n_points=int(10_000_000 * scale))
+    if name == "country":
+        return W.country(seed=W.BASE_SEED + 6 + 1000 * rank, n_points=max(1, int(W.PAPER_N_POINTS * scale)))
     raise SystemExit(f"unknown workload {name}")
 
 
@@ -240,14 +254,14 @@ def run_reference(args, rank, world):
     import oracle
     oracle.build()
     w = make_workload(args.workload, 0, 1.0)
-    # a bounded sample: the first polygons of the batch, sized so that warm-up plus timed
-    # steps take about two minutes of CPU work in total
+    # a bounded sample: the leading polygons (or points, in dense mode) of the batch, sized from
+    # a short probe so that warm-up plus timed steps take about two minutes of CPU work in total
     threads = oracle.default_threads()
+    probe = w.bounded(2e8)
     t0 = time.perf_counter()
-    oracle.classify(w.points, w.poly_offsets, w.verts, w.cand_offsets, w.cand_ids, threads=threads)
-    t_full = time.perf_counter() - t0
-    frac = min(1.0, 120.0 / max(1e-9, (args.steps + args.warmup) * t_full))
-    sub = w.prefix(max(1, int(w.n_polys * frac)))
+    oracle.classify(probe.points, probe.poly_offsets, probe.verts, probe.cand_offsets, probe.cand_ids, threads=threads)
+    rate = probe.pair_tests() / max(1e-9, time.perf_counter() - t0)
+    sub = w.bounded(rate * 120.0 / max(1, args.steps + args.warmup))
     steps_t = []
     for i in range(args.warmup + args.steps):
         t0 = time.perf_counter()
@@ -264,8 +278,8 @@ def run_reference(args, rank, world):
             "data": "synthetic", "config": {"workload": f"{w.name}: {w.n_polys} polygons, {w.n_candidates} candidates",
                                              "pair_tests_per_step": T, "l2": "inputs larger than L2"},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
-                             "sample": f"first {sub.n_polys} of {w.n_polys} {w.name} polygons per step "
-                                       f"({sub.n_candidates} candidates, {T} pair tests)"},
+                             "sample": f"leading part of the {w.name} batch per step: {sub.n_polys} of {w.n_polys} "
+                                       f"polygons, {sub.n_candidates} candidates, {T} pair tests"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
             "points_per_s": sub.n_candidates * len(steps_t) / tot}
     print(json.dumps(line), flush=True)
@@ -397,7 +411,7 @@ def main():
     ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="footprints", choices=["footprints", "stress", "star", "fractal", "join"])
+    ap.add_argument("--workload", default="footprints", choices=["footprints", "stress", "star", "fractal", "join", "country"])
     ap.add_argument("--kernel", default="filtered", choices=["filtered", "exact"])
     ap.add_argument("--semantics", default="halfopen", choices=["halfopen", "alg1", "alg2"],
                     help="alg1/alg2: time the paper's printed Algorithm 1 or 2 (pip_classify_paper) and "

@@ -3,7 +3,7 @@
 Shared by the tests, the benchmark and the oracle checks.  Coordinates are int32
 fixed point in 1e-7 degree units.  The paper's own data (Google Open Buildings points
 for Ghana against the GADM Ghana polygon, Simulation section) is not available, so
-these generators stand in for it with the shapes, sizes and distributions of the five
+these generators stand in for it with the shapes, sizes and distributions of the six
 workloads listed in ``WORKLOADS``:
 
 1. ``star``        one 1,024-vertex star polygon, R = 1e5 units; 100,000 uniform points in
@@ -21,6 +21,9 @@ workloads listed in ``WORKLOADS``:
 5. ``stress``      1M polygons of 3-32 vertices spanning the whole int32 range (needle
                    triangles, collinear runs, random stars), 8 points per polygon, half of
                    them placed on or within 1-3 units of the boundary.
+6. ``country``     the paper's experiment in shape: 17,097,823 building-like points (70% in
+                   1,000 settlements) against one 100,000-vertex fractal country-like polygon
+                   spanning the box; dense mode.
 
 Seeds: ``seed_k = 2306043160 + k`` (numpy PCG64) unless a test passes its own.
 """
@@ -108,6 +111,17 @@ class Workload:
         co = self.cand_offsets[:n + 1]
         return dataclasses.replace(self, poly_offsets=po, verts=v, cand_offsets=co,
                                    cand_ids=self.cand_ids[:int(co[-1])] if n else self.cand_ids[:0])
+
+    def bounded(self, max_pairs: float) -> "Workload":
+        """A leading part of the batch with at most about max_pairs pair tests (at least one
+        polygon or point): the first polygons (CSR), or the first points (dense)."""
+        T = self.pair_tests()
+        if T <= max_pairs:
+            return self
+        if self.dense:
+            n = max(1, int(self.n_points * max_pairs / T))
+            return dataclasses.replace(self, points=self.points[:n])
+        return self.prefix(max(1, int(self.n_polys * max_pairs / T)))
 
     def with_csr(self, cand_offsets, cand_ids, name=None):
         return dataclasses.replace(self, name=name or self.name,
@@ -477,12 +491,39 @@ def stress(seed=BASE_SEED + 5, n_polys=1_000_000, pts_per_poly=8) -> Workload:
                     meta=dict(seed=seed, n_polys=n_polys, pts_per_poly=pts_per_poly))
 
 
+# ---------------------------------------------------------------------------------------------
+# 6. paper-shaped: all building points of the country against its boundary polygon
+# ---------------------------------------------------------------------------------------------
+
+PAPER_N_POINTS = 17_097_823   # building points left in Ghana's box (Simulation section)
+
+
+def country(seed=BASE_SEED + 6, m=100_000, n_points=PAPER_N_POINTS, n_clusters=1_000) -> Workload:
+    """One country-like polygon against every building point in its box, as in the paper's
+    experiment (Simulation section: the Open Buildings points inside Ghana's box against the
+    GADM boundary of Ghana).  Neither data set is available, so: the polygon is a fractal
+    coastline (midpoint displacement from an octagon, Hurst 0.7) with m vertices (the paper
+    does not state the boundary's vertex count; 1e5 is an assumption) spanning most of the
+    lon/lat box; the points are building-like, 70 % in 1,000 Gaussian settlements of sigma
+    200 m and 30 % uniform in the box.  Dense mode: every point is a candidate."""
+    rng = _rng(seed)
+    cx, cy = (LON0 + LON1) / 2.0, (LAT0 + LAT1) / 2.0
+    r = 0.45 * min(LON1 - LON0, LAT1 - LAT0)
+    p = _midpoint_displacement(rng, m, (cx, cy), r, 0.05 * r)
+    v = _clip32(np.clip(np.rint(p), [LON0, LAT0], [LON1, LAT1])).astype(np.int64)
+    clusters = np.stack([rng.uniform(LON0, LON1, n_clusters), rng.uniform(LAT0, LAT1, n_clusters)], 1)
+    pts = _clip32(_clustered(rng, n_points, clusters, 200.0, 0.7))
+    return Workload("country", pts.astype(np.int32), np.array([0, m], dtype=np.int32), v.astype(np.int32),
+                    meta=dict(seed=seed, m=m, n_points=n_points, n_clusters=n_clusters))
+
+
 WORKLOADS = {
     "star": star,
     "footprints": footprints,
     "join": join,
     "fractal": fractal,
     "stress": stress,
+    "country": country,
 }
 
 

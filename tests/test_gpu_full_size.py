@@ -66,3 +66,15 @@ def test_join_full_size_sampled(api):
         order = np.argsort(ids[seg], kind="stable")
         assert np.array_equal(ids[seg][order], want_ids[sub_co[i]:sub_co[i + 1]]), f"candidates of polygon {k}"
         assert np.array_equal(bits[seg][order], want_bits[sub_co[i]:sub_co[i + 1]]), f"bits of polygon {k}"
+
+
+def test_country_full_size_sampled(api):
+    """The paper-shaped batch: 17,097,823 building-like points against one 100,000-vertex
+    country-like polygon (dense mode), checked on 3,000 sampled points."""
+    w = W.country()
+    rng = np.random.default_rng(2306043160 + 79)
+    sample = np.unique(rng.integers(0, w.n_points, 3000))
+    want = oracle.classify_sample(w.points, w.poly_offsets, w.verts, sample)
+    got = oracle.unpack_bits(gpu_bits(api, w), w.n_bits)[sample]
+    bad = np.nonzero(got != want)[0]
+    assert len(bad) == 0, f"{len(bad)} of {len(sample)} sampled bits differ"
