@@ -26,8 +26,8 @@ struct DeviceState {
 std::mutex g_mu;
 DeviceState g_dev[MAX_DEVICES];
 std::atomic<int> g_edge_tile{2048};
-std::atomic<int> g_ctas{4};
-std::atomic<int> g_ppt{2};
+std::atomic<int> g_ctas{3};
+std::atomic<int> g_ppt{4};
 std::atomic<unsigned long long> g_launches{0};
 std::atomic<int> g_verify{0};
 thread_local int g_last_cuda = 0;

@@ -568,6 +568,63 @@ __device__ __forceinline__ void tile_parity_multi(const float4 *__restrict__ s_r
     }
 }
 
+// The same for a tile whose frame is below 2^30 from its centre, with scaled records: edge e is
+// (-c' s_e, |d_y| s_e, -s d_x s_e, y_{e+1}) with s_e = 2^-k_e >= 1 / (M_x |d_y| + M_y |d_x|), so
+// that nt = fma(P_y, ., fma(P_x, ., .)) = -s det s_e (rounded) and the edge's bound scaled by
+// s_e is at most 13u whatever the edge: |nt| < 13u is the one uncertainty test.  The straddle
+// test is the sign bit of (p_y - y_e) ^ (p_y - y_{e+1}) (the frame is under 2^31 tall), and an
+// edge counts when that bit and nt's sign bit are both set.  All PPT candidates share each record
+// load; each keeps its parity and its uncertainty in a sign bit.
+template <int PPT, bool VERIFY>
+__device__ __forceinline__ void tile_parity_scaled(const int4 *__restrict__ s_rec, const int2 *__restrict__ s_v,
+                                                   int nt, const int2 (&p)[PPT], const bool (&ok)[PPT], int ox,
+                                                   int oy, int (&par)[PPT], unsigned long long &n_fb_pts,
+                                                   unsigned long long &n_err, unsigned long long &n_ver)
+{
+    float Px[PPT], Py[PPT];
+    unsigned py[PPT], up[PPT], acc[PPT], unc[PPT];
+    const unsigned y0 = (unsigned)s_v[0].y;
+    #pragma unroll
+    for (int r = 0; r < PPT; ++r) {
+        Px[r] = __int2float_rn(p[r].x - ox);
+        Py[r] = __int2float_rn(p[r].y - oy);
+        py[r] = (unsigned)p[r].y;
+        up[r] = py[r] - y0;
+        acc[r] = 0;
+        unc[r] = 0;
+    }
+    #pragma unroll 2
+    for (int e = 0; e < nt; ++e) {
+        const int4 q = s_rec[e];
+        const float rc = __int_as_float(q.x), ra = __int_as_float(q.y), rb = __int_as_float(q.z);
+        #pragma unroll
+        for (int r = 0; r < PPT; ++r) {
+            const unsigned u = py[r] - (unsigned)q.w;
+            const unsigned x = u ^ up[r];
+            up[r] = u;
+            const float ntf = __fmaf_rn(Py[r], rb, __fmaf_rn(Px[r], ra, rc));
+            const float d = fabsf(ntf) - PM_BOUND_K;   // negative exactly when |nt| < 13u
+            if (VERIFY && ok[r] && (int)x < 0 && d >= 0.f) {   // a trusted FP32 sign: its exact test
+                const int2 ri = s_v[e], rj = s_v[e + 1];
+                n_err += exact_edge_counts(p[r].x, p[r].y, ri.x, ri.y, rj.x, rj.y) != (int)(__float_as_uint(ntf) >> 31);
+                ++n_ver;
+            }
+            acc[r] ^= x & __float_as_uint(ntf);
+            unc[r] |= x & __float_as_uint(d);
+        }
+    }
+    #pragma unroll
+    for (int r = 0; r < PPT; ++r) {
+        if (!ok[r]) continue;
+        int pr = (int)(acc[r] >> 31);
+        if (unc[r] >> 31) {
+            ++n_fb_pts;
+            pr = exact_parity(s_v, 0, nt, false, p[r]);
+        }
+        par[r] ^= pr;
+    }
+}
+
 // Edges per work item of a large polygon with m edges and nb candidate blocks: slices short
 // enough that the listed polygons give every CTA about two items, never below 256 edges or
 // above 16,384, a multiple of 32.  Every CTA derives the same value.
@@ -717,23 +774,32 @@ __global__ void __launch_bounds__(LG_THREADS) k_pip_large(ClassifyArgs a, long l
             const float fMx = __uint2float_ru(Mx), fMy = __uint2float_ru(My);
             for (int i = tid; i < nt; i += LG_THREADS) {
                 const int2 ri = s_v[i], rj = s_v[i + 1];
+                const long long ady = llabs((long long)rj.y - ri.y), adx = llabs((long long)rj.x - ri.x);
+                // M_x |d_y| + M_y |d_x|, rounded up
+                const float S = __fadd_ru(__fmul_ru(fMx, __ll2float_ru(ady)), __fmul_ru(fMy, __ll2float_ru(adx)));
                 float4 rec;
                 if (!wide) {
                     const int dx = rj.x - ri.x, dy = rj.y - ri.y;
                     const float fdx = __int2float_rn(dx), fdy = __int2float_rn(dy);
                     const float X = __int2float_rn(ri.x - ox), Y = __int2float_rn(ri.y - oy);
                     const float c = __fmaf_rn(X, fdy, -__fmul_rn(Y, fdx));
-                    rec = dy > 0 ? make_float4(c, fdy, fdx, 0.f) : make_float4(-c, -fdy, -fdx, 0.f);
+                    // s_e = 2^-k with 2^k >= S (exact scaling: a power of two)
+                    const unsigned eb = (__float_as_uint(S) >> 23) & 0xffu;
+                    const float se = S > 0.f ? __uint_as_float((253u - eb) << 23) : 1.f;
+                    rec = dy > 0 ? make_float4(-c * se, fdy * se, -fdx * se, __int_as_float(rj.y))
+                                 : make_float4(c * se, -fdy * se, fdx * se, __int_as_float(rj.y));
                 } else {
                     rec = wide_record(ri, rj, ox, oy);
+                    rec.w = __fmul_ru(PM_BOUND_K, S);   // the edge's own bound 13u (M_x |d_y| + M_y |d_x|)
                 }
-                // the edge's own bound 13u (M_x |d_y| + M_y |d_x|) (see PM_BOUND_K)
-                const long long ady = llabs((long long)rj.y - ri.y), adx = llabs((long long)rj.x - ri.x);
-                rec.w = __fmul_ru(PM_BOUND_K, __fadd_ru(__fmul_ru(fMx, __ll2float_ru(ady)), __fmul_ru(fMy, __ll2float_ru(adx))));
                 s_rec[i] = rec;
             }
             __syncthreads();
-            tile_parity_multi<PPT, VERIFY>(s_rec, s_v, nt, pt, ok, ox, oy, par, st_fbp, st_err, st_ver);
+            if (!wide)
+                tile_parity_scaled<PPT, VERIFY>(reinterpret_cast<const int4 *>(s_rec), s_v, nt, pt, ok, ox, oy, par,
+                                                st_fbp, st_err, st_ver);
+            else
+                tile_parity_multi<PPT, VERIFY>(s_rec, s_v, nt, pt, ok, ox, oy, par, st_fbp, st_err, st_ver);
             __syncthreads();
         }
         // XOR the partial parities into the output words (the block need not be word-aligned)

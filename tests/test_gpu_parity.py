@@ -152,7 +152,7 @@ def test_many_empty_polygons_in_one_chunk(api):
     check_full(api, make("sparse-csr", polys, pts, csr))
 
 
-@pytest.mark.parametrize("tuning", [(256, 1, 1), (512, 2, 2), (1024, 4, 2), (2048, 2, 4), (8192, 1, 1)])
+@pytest.mark.parametrize("tuning", [(256, 1, 1), (512, 2, 2), (1024, 4, 2), (2048, 2, 4), (2048, 4, 3), (8192, 1, 1)])
 def test_tuning_shapes(api, tuning):
     """Every tuned shape gives the same bits (small edge tiles force the streamed path)."""
     before = api.pip_get_tuning()
@@ -323,6 +323,42 @@ def test_full_range_boxes_points_on_extremes(api):
     ids = list(range(len(pts)))
     check_full(api, make("full-range-csr", polys, pts, [ids] * len(polys)))
     check_full(api, make("full-range-dense", polys, pts))
+
+
+def _star_polygon(rng, m, radius, centre=(0, 0)):
+    ang = np.sort(rng.uniform(0, 2 * np.pi, m))
+    rad = rng.uniform(0.5, 1.0, m) * radius
+    v = np.stack([centre[0] + rad * np.cos(ang), centre[1] + rad * np.sin(ang)], 1)
+    return np.clip(np.rint(v), -2**31, 2**31 - 1).astype(np.int64)
+
+
+def test_large_polygons_full_range_and_near_the_frame_limit(api):
+    """Large-polygon kernel tiles whose frame reaches 2^30 from its centre or more (int64 and
+    double records, edge-by-edge bounds) and tiles just below that limit (scaled records, the
+    sign-bit straddle test); points uniform, on vertices, on edge midpoints and at the extremes."""
+    rng = np.random.default_rng(2306043160 + 81)
+    polys = [_star_polygon(rng, 2000, 2.0**31), _star_polygon(rng, 1500, 2.0**29.95),
+             _star_polygon(rng, 700, 2.0**30.2, centre=(2.0**30, -2.0**30))]
+    pts = [rng.integers(-2**31, 2**31, (3000, 2), endpoint=False)]
+    for v in polys:
+        pts.append(v[rng.integers(0, len(v), 200)])
+        a, b = v, np.roll(v, -1, axis=0)
+        even = ((a + b) % 2 == 0).all(axis=1)
+        pts.append(((a + b) // 2)[even][:200])
+    lo, hi = -2**31, 2**31 - 1
+    pts.append(np.array([(lo, lo), (hi, hi), (lo, hi), (hi, lo), (0, 0), (hi, 0), (0, lo)]))
+    pts = np.concatenate(pts).astype(np.int64)
+    w = make("large-full-range", [v.tolist() for v in polys], pts.tolist())
+    check_full(api, w)
+    api.pip_set_verify(True)
+    try:
+        api.pip_reset_stats()
+        got = gpu_bits(api, w)
+        s = api.pip_get_stats()
+    finally:
+        api.pip_set_verify(False)
+    assert_same(got, oracle.classify(w.points, w.poly_offsets, w.verts), w.n_bits, "verification mode")
+    assert s["verified_pairs"] > 0 and s["filter_errors"] == 0
 
 
 # ------------------------------------------------------------------------------------------
