@@ -129,6 +129,41 @@ int pip_classify_paper(const int32_t *points, int64_t n_points,
                        uint32_t *out_bits, void *stream);
 
 /*
+ * y-slab edge index (not in the paper: a step beside the method that changes how many pair
+ * tests a point needs, not its answer).  Every polygon with more than 256 vertices gets
+ * about m / edges_per_slab slabs of equal height over its y-range (no lower than its mean edge
+ * height); each edge is listed in every
+ * slab its y-range [min y, max y) meets, or, when it meets more than 8, once in the polygon's
+ * list of tall edges.  A point then tests only its slab's edges and the tall list -- exactly
+ * the edges that can straddle its ray -- with the exact 64/128-bit side test, so the bits equal
+ * pip_classify's while a point of a 100,000-vertex polygon tests tens of edges, not 100,000.
+ *
+ * pip_slab_index_bytes: size of an index buffer for n_polys polygons with n_verts vertices in
+ * all that holds `capacity` (edge, slab) entries (0 on a bad argument).  Typical data needs 1-2
+ * entries per vertex of the slabbed polygons; a build reports the exact number.
+ *
+ * pip_slab_build: builds the index of (poly_offsets, verts) into `index` (device, caller-owned,
+ * 256-byte aligned, index_bytes long) on `stream`, and writes the number of entries the
+ * polygons need to *d_entries (device int64, may be NULL).  If they exceed the buffer's
+ * capacity the index is marked unusable (pip_classify_slab then ignores it and classifies as
+ * pip_classify does); rebuild with a larger buffer.  edges_per_slab in 1..256 (8 is a good
+ * default).  Returns PIP_OK, PIP_ERR_INVALID, PIP_ERR_WORKSPACE (buffer smaller than its fixed
+ * part), or another PIP_ERR_*.
+ *
+ * pip_classify_slab: pip_classify (same arguments, output and small-polygon kernel) with
+ * `slab_index` (device, built by pip_slab_build for the same poly_offsets and verts, or NULL)
+ * used for the polygons it covers.
+ */
+size_t pip_slab_index_bytes(int32_t n_polys, int64_t n_verts, int32_t edges_per_slab, int64_t capacity);
+int pip_slab_build(const int32_t *poly_offsets, const int32_t *verts, int32_t n_polys, int64_t n_verts,
+                   int32_t edges_per_slab, void *index, size_t index_bytes, int64_t *d_entries,
+                   void *stream);
+int pip_classify_slab(const int32_t *points, int64_t n_points,
+                      const int32_t *poly_offsets, const int32_t *verts, int32_t n_polys,
+                      const int32_t *cand_offsets, const int32_t *cand_ids, const void *slab_index,
+                      uint32_t *out_bits, void *stream);
+
+/*
  * pip_classify_noalloc -- pip_classify for callers that cannot allocate device memory (the
  * paper has no counterpart).  pip_classify allocates, on its first call on each stream, the
  * device list that hands large polygons to its second kernel (and, once per device, its

@@ -14,7 +14,7 @@ import torch
 
 from . import _lib
 
-__all__ = ["pip_classify", "pip_classify_exact", "pip_classify_paper", "pip_classify_noalloc", "pip_bin_count", "pip_bin_fill", "bin_join",
+__all__ = ["pip_classify", "pip_classify_exact", "pip_classify_paper", "pip_classify_slab", "slab_index", "pip_classify_noalloc", "pip_bin_count", "pip_bin_fill", "bin_join",
            "pip_set_tuning", "pip_get_tuning", "pip_get_stats", "pip_reset_stats", "pip_launch_count", "pip_set_verify", "pip_validate",
            "out_words", "to_device"]
 
@@ -96,6 +96,41 @@ def pip_classify_paper(points, poly_offsets, verts, cand_offsets=None, cand_ids=
     """The paper's Algorithm 1 or 2 evaluated literally (``pip_classify_paper``)."""
     return _classify("pip_classify_paper", points, poly_offsets, verts, cand_offsets, cand_ids, out,
                      n_cands, stream, extra=(int(algorithm),))
+
+
+def slab_index(poly_offsets, verts, edges_per_slab=8, stream=None):
+    """Build the y-slab edge index of the polygons (``pip_slab_build``) in a new device buffer,
+    rebuilding once with the exact size if the first estimate (2 entries per vertex) was short.
+    Returns the uint8 buffer; pass it to ``pip_classify_slab``."""
+    lib = _lib.load()
+    _need(poly_offsets, "poly_offsets")
+    _need(verts, "verts", 2)
+    n_polys = int(poly_offsets.shape[0]) - 1
+    n_verts = int(verts.shape[0])
+    need = torch.zeros(1, dtype=torch.int64, device=verts.device)
+    cap = 2 * n_verts + 1024
+    for _ in range(2):
+        nbytes = int(lib.pip_slab_index_bytes(n_polys, n_verts, int(edges_per_slab), cap))
+        if nbytes == 0:
+            raise ValueError("bad slab index arguments")
+        index = torch.empty(nbytes, dtype=torch.uint8, device=verts.device)
+        _lib.check("pip_slab_build", lib.pip_slab_build(_ptr(poly_offsets), _ptr(verts), n_polys, n_verts,
+                                                         int(edges_per_slab), _ptr(index), nbytes, _ptr(need),
+                                                         _stream(stream)))
+        n = int(need.item())
+        if n <= cap:
+            return index
+        cap = n
+    return index
+
+
+def pip_classify_slab(points, poly_offsets, verts, cand_offsets=None, cand_ids=None, index=None, out=None,
+                      n_cands=None, stream=None):
+    """``pip_classify`` with a y-slab index (``slab_index``) for the large polygons."""
+    if index is not None and not (index.is_cuda and index.is_contiguous()):
+        raise ValueError("index must be the contiguous CUDA buffer returned by slab_index")
+    return _classify("pip_classify_slab", points, poly_offsets, verts, cand_offsets, cand_ids, out,
+                     n_cands, stream, extra=(_ptr(index),))
 
 
 def pip_classify_noalloc(points, poly_offsets, verts, cand_offsets=None, cand_ids=None, out=None,

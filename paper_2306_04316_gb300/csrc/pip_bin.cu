@@ -49,7 +49,7 @@ struct BinLayout {
 
 static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
-static long long scan_tmp_elems(long long n)
+long long scan_tmp_elems(long long n)
 {
     long long t = 0;
     while (n > SCAN_TILE) {
@@ -130,7 +130,7 @@ __global__ void k_scan_add(unsigned *d, long long n, const unsigned *block_sums)
         if (base + i < n) d[base + i] += add;
 }
 
-static int scan_exclusive(unsigned *d, long long n, unsigned *tmp, cudaStream_t s)
+int scan_exclusive(unsigned *d, long long n, unsigned *tmp, cudaStream_t s)
 {
     const long long nb = (n + SCAN_TILE - 1) / SCAN_TILE;
     if (nb <= 1) {

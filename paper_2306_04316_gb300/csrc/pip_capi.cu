@@ -126,6 +126,7 @@ ClassifyArgs make_args(const int32_t *points, int64_t n_points, const int32_t *p
     a.out_bits = out_bits;
     a.words_per_poly = (n_points + 31) / 32;
     a.stats = stats;
+    a.slab = nullptr;
     return a;
 }
 
@@ -143,8 +144,17 @@ int pip_classify(const int32_t *points, int64_t n_points, const int32_t *poly_of
                  const int32_t *verts, int32_t n_polys, const int32_t *cand_offsets,
                  const int32_t *cand_ids, uint32_t *out_bits, void *stream)
 {
+    return pip_classify_slab(points, n_points, poly_offsets, verts, n_polys, cand_offsets, cand_ids, nullptr,
+                             out_bits, stream);
+}
+
+int pip_classify_slab(const int32_t *points, int64_t n_points, const int32_t *poly_offsets,
+                      const int32_t *verts, int32_t n_polys, const int32_t *cand_offsets,
+                      const int32_t *cand_ids, const void *slab_index, uint32_t *out_bits, void *stream)
+{
     int rc = check_classify(points, n_points, poly_offsets, verts, n_polys, cand_offsets, cand_ids, out_bits);
     if (rc != PIP_OK) return rc;
+    if (misaligned(slab_index, 256)) return PIP_ERR_ALIGN;
     if (n_polys == 0) return PIP_OK;
     const bool dense = cand_offsets == nullptr;
     const long long total_bits = dense ? (long long)n_polys * 32 * ((n_points + 31) / 32) : 0;
@@ -158,8 +168,34 @@ int pip_classify(const int32_t *points, int64_t n_points, const int32_t *poly_of
     if (rc != PIP_OK) return rc;
     ClassifyArgs a = make_args(points, n_points, poly_offsets, verts, n_polys, cand_offsets, cand_ids,
                                out_bits, ds->stats);
+    a.slab = static_cast<const unsigned char *>(slab_index);
     Tuning t = current_tuning();
     int e = launch_filtered(a, total_bits, t, ds->n_sm, ll, LARGE_LIST_CAP, s);
+    return e == 0 ? PIP_OK : cuda_fail((cudaError_t)e);
+}
+
+size_t pip_slab_index_bytes(int32_t n_polys, int64_t n_verts, int32_t edges_per_slab, int64_t capacity)
+{
+    if (n_polys < 0 || n_verts < 0 || edges_per_slab < 1 || edges_per_slab > 256 || capacity < 0) return 0;
+    return slab_index_bytes(n_polys, n_verts, edges_per_slab, capacity);
+}
+
+int pip_slab_build(const int32_t *poly_offsets, const int32_t *verts, int32_t n_polys, int64_t n_verts,
+                   int32_t edges_per_slab, void *index, size_t index_bytes, int64_t *d_entries, void *stream)
+{
+    if (n_polys < 0 || n_verts < 0) return PIP_ERR_SIZE;
+    if (edges_per_slab < 1 || edges_per_slab > 256) return PIP_ERR_INVALID;
+    if (!index || (n_polys > 0 && (!poly_offsets || !verts))) return PIP_ERR_NULL;
+    if (n_verts > (int64_t)INT_MAX) return PIP_ERR_TOO_LARGE;
+    if (misaligned(index, 256) || misaligned(verts, 8) || misaligned(poly_offsets, 4) || misaligned(d_entries, 8))
+        return PIP_ERR_ALIGN;
+    if (index_bytes < slab_index_bytes(n_polys, n_verts, edges_per_slab, 0)) return PIP_ERR_WORKSPACE;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    DeviceState *ds = nullptr;
+    int rc = device_state(s, &ds);
+    if (rc != PIP_OK) return rc;
+    int e = launch_slab_build(poly_offsets, reinterpret_cast<const int2 *>(verts), n_polys, n_verts, edges_per_slab,
+                              index, index_bytes, reinterpret_cast<long long *>(d_entries), ds->n_sm, s);
     return e == 0 ? PIP_OK : cuda_fail((cudaError_t)e);
 }
 

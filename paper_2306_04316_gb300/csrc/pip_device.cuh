@@ -57,6 +57,25 @@ __device__ __forceinline__ void cp_async4(void *smem_dst, const void *gmem_src)
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
+// y-slab edge index of the large polygons (see pip_slab.cu).  The index is one caller-owned
+// device buffer: this header, then per polygon (y0, h, S, 0) (S slabs of height h from y0; S = 0
+// for polygons without slabs), the first slab of each polygon, the first entry of each slab, a
+// scratch array of per-slab cursors and scan space, and the entries: one (x_i, y_i, x_j, y_j) per
+// (edge, slab) whose y-range [min y, max y) meets the slab.  Slab S of a polygon holds its tall
+// edges (those meeting more than SLAB_TALL slabs), which every point of the polygon tests.
+constexpr int SLAB_MIN_M = 257;     // polygons with more vertices get slabs
+constexpr int SLAB_TALL = 8;
+struct SlabHeader {
+    int valid;                      // 1 when the build completed and every entry fitted
+    int n_polys;
+    int edges_per_slab;
+    int pad0;
+    long long n_slabs;              // slab bound used by the layout (tall lists included)
+    long long n_entries;            // entries the polygons need
+    long long capacity;             // entries the buffer holds
+    long long off_geom, off_slab, off_entry, off_cursor, off_scan, off_entries;
+};
+
 struct ClassifyArgs {
     const int2 *points;
     long long n_points;
@@ -68,6 +87,7 @@ struct ClassifyArgs {
     uint32_t *out_bits;
     long long words_per_poly;      // dense mode: W = ceil(n_points / 32)
     unsigned long long *stats;     // device counters (may be nullptr)
+    const unsigned char *slab;     // y-slab index of the large polygons (may be nullptr)
 };
 
 // |v| < 2^31, so that products of two such values fit in 62 bits.

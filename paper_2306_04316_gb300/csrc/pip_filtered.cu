@@ -625,6 +625,32 @@ __device__ __forceinline__ void tile_parity_scaled(const int4 *__restrict__ s_re
     }
 }
 
+// Parity of p against polygon k through its y-slab index: the edges of p's slab and the tall
+// list are exactly the edges whose y-range [min y, max y) contains p_y, i.e. every edge that can
+// straddle p's ray; each straddling one is decided with the exact 64/128-bit test.
+__device__ __forceinline__ int slab_parity(const unsigned char *ix, const SlabHeader *sh, int k, int2 p)
+{
+    const int4 g = reinterpret_cast<const int4 *>(ix + sh->off_geom)[k];
+    if (p.y < g.x) return 0;
+    const unsigned s = ((unsigned)p.y - (unsigned)g.x) / (unsigned)g.y;
+    if (s >= (unsigned)g.z) return 0;                 // above the polygon: no edge straddles
+    const unsigned *so = reinterpret_cast<const unsigned *>(ix + sh->off_slab);
+    const unsigned *eo = reinterpret_cast<const unsigned *>(ix + sh->off_entry);
+    const int4 *en = reinterpret_cast<const int4 *>(ix + sh->off_entries);
+    const unsigned b = __ldg(so + k);
+    int parity = 0;
+    #pragma unroll 1
+    for (int pass = 0; pass < 2; ++pass) {            // p's slab, then the tall list
+        const unsigned sl = b + (pass == 0 ? s : (unsigned)g.z);
+        const unsigned e1 = __ldg(eo + sl + 1);
+        for (unsigned e = __ldg(eo + sl); e < e1; ++e) {
+            const int4 q = __ldg(en + e);
+            if ((q.y > p.y) != (q.w > p.y)) parity ^= exact_edge_counts(p.x, p.y, q.x, q.y, q.z, q.w);
+        }
+    }
+    return parity;
+}
+
 // Edges per work item of a large polygon with m edges and nb candidate blocks: slices short
 // enough that the listed polygons give every CTA about two items, never below 256 edges or
 // above 16,384, a multiple of 32.  Every CTA derives the same value.
@@ -638,7 +664,7 @@ __device__ __forceinline__ int slice_edges(long long m, long long nb, int nlarge
 }
 
 template <int PPT, bool VERIFY>
-__global__ void __launch_bounds__(LG_THREADS) k_pip_large(ClassifyArgs a, long long total_bits, LargeList *ll,
+__global__ void __launch_bounds__(LG_THREADS, PPT == 4 ? 3 : 4) k_pip_large(ClassifyArgs a, long long total_bits, LargeList *ll,
                                                          int lcap, int T)
 {
     extern __shared__ __align__(16) unsigned char dsm[];
@@ -658,6 +684,17 @@ __global__ void __launch_bounds__(LG_THREADS) k_pip_large(ClassifyArgs a, long l
     const bool scan = *((volatile int *)&ll->overflow) != 0;
     if (count == 0 && !scan) return;   // nothing listed: the header is already clear for the next call
     long long scan_k = blockIdx.x;   // overflow mode: polygons blockIdx.x, + gridDim.x, ...
+    const SlabHeader *sh = reinterpret_cast<const SlabHeader *>(a.slab);
+    const bool slab_ok = sh && sh->valid && sh->n_polys == P;
+    // polygons with a y-slab index: one item per candidate block, no edge slices
+    auto slabbed = [&](int k) {
+        return slab_ok && reinterpret_cast<const int4 *>(a.slab + sh->off_geom)[k].z > 0;
+    };
+    // candidates per slab item: PPT per thread while the listed polygons give every CTA several
+    // items that way, else one per thread (more, smaller items)
+    auto slab_block = [&](long long n_cand) -> long long {
+        return (n_cand / CB) * max(count, 1) >= 2LL * gridDim.x ? CB : LG_THREADS;
+    };
     int scan_item = 0;
 
     while (true) {
@@ -671,8 +708,10 @@ __global__ void __launch_bounds__(LG_THREADS) k_pip_large(ClassifyArgs a, long l
                     const long long cs = dense ? k * W32 : (long long)a.cand_offsets[k];
                     const long long ce = dense ? cs + W32 : (long long)a.cand_offsets[k + 1];
                     const long long m = (long long)a.poly_offsets[k + 1] - a.poly_offsets[k];
-                    const long long nb = (ce - cs + CB - 1) / CB;
-                    const int ES = slice_edges(m, nb, count, gridDim.x);
+                    const bool sl = slabbed(k);
+                    const long long cbk = sl ? slab_block(ce - cs) : CB;
+                    const long long nb = (ce - cs + cbk - 1) / cbk;
+                    const int ES = sl ? (int)max(m, 1LL) : slice_edges(m, nb, count, gridDim.x);
                     const long long ns = (m + ES - 1) / ES;
                     const int it = atomicAdd(large_taken(ll, lcap) + e, 1);
                     if ((long long)it < nb * ns) {
@@ -688,8 +727,10 @@ __global__ void __launch_bounds__(LG_THREADS) k_pip_large(ClassifyArgs a, long l
                     const long long ce = dense ? cs + W32 : (long long)a.cand_offsets[k + 1];
                     const long long m = (long long)a.poly_offsets[k + 1] - a.poly_offsets[k];
                     const long long n = dense ? min((long long)a.n_points, W32) : ce - cs;
-                    const long long nb = is_large_polygon(m, n) ? (ce - cs + CB - 1) / CB : 0;
-                    const int ES = slice_edges(m, nb, count, gridDim.x);
+                    const bool sl = slabbed(k);
+                    const long long cbk = sl ? slab_block(ce - cs) : CB;
+                    const long long nb = is_large_polygon(m, n) ? (ce - cs + cbk - 1) / cbk : 0;
+                    const int ES = sl ? (int)max(m, 1LL) : slice_edges(m, nb, count, gridDim.x);
                     const long long ns = (m + ES - 1) / ES;
                     if (scan_item < nb * ns) {
                         s_item[0] = k; s_item[1] = (int)(scan_item / ns); s_item[2] = (int)(scan_item % ns);
@@ -707,7 +748,9 @@ __global__ void __launch_bounds__(LG_THREADS) k_pip_large(ClassifyArgs a, long l
         const int k = s_item[0];
         const long long cs = dense ? k * W32 : (long long)a.cand_offsets[k];
         const long long ce = dense ? cs + W32 : (long long)a.cand_offsets[k + 1];
-        const long long cb0 = cs + (long long)s_item[1] * CB, cb1 = min(cb0 + CB, ce);
+        const bool use_slabs = slabbed(k);
+        const long long cbk = use_slabs ? slab_block(ce - cs) : CB;
+        const long long cb0 = cs + (long long)s_item[1] * cbk, cb1 = min(cb0 + cbk, ce);
         const int base = a.poly_offsets[k];
         const int m = a.poly_offsets[k + 1] - base;
         const int ES = s_item[3];
@@ -734,8 +777,13 @@ __global__ void __launch_bounds__(LG_THREADS) k_pip_large(ClassifyArgs a, long l
                 if (s_item[2] == 0) ++st_cand;
             }
         }
+        if (use_slabs) {
+            #pragma unroll
+            for (int r = 0; r < PPT; ++r)
+                if (ok[r]) par[r] = slab_parity(a.slab, sh, k, pt[r]);
+        }
         __syncthreads();
-        for (int e0 = ea; s_pb[0] <= s_pb[2] && e0 < eb; e0 += T) {
+        for (int e0 = ea; !use_slabs && s_pb[0] <= s_pb[2] && e0 < eb; e0 += T) {
             const int nt = min(T, eb - e0);
             if (tid == 0) { s_tb[0] = s_pb[0]; s_tb[1] = s_pb[1]; s_tb[2] = s_pb[2]; s_tb[3] = s_pb[3]; }
             for (int i = tid; i <= nt; i += LG_THREADS) {

@@ -30,6 +30,16 @@ Tuning current_tuning();   // the values set by pip_set_tuning
 int launch_validate(const ClassifyArgs &a, long long n_verts, long long n_cand_ids, int *d_status, int grid,
                     cudaStream_t stream);
 
+// exclusive scan of uint32 in place (multi-level); tmp holds scan_tmp_elems(n) values
+long long scan_tmp_elems(long long n);
+int scan_exclusive(unsigned *d, long long n, unsigned *tmp, cudaStream_t s);
+
+// y-slab edge index
+size_t slab_index_bytes(int n_polys, long long n_verts, int edges_per_slab, long long capacity);
+int launch_slab_build(const int32_t *poly_offsets, const int2 *verts, int n_polys, long long n_verts,
+                      int edges_per_slab, void *index, size_t index_bytes, long long *d_entries, int n_sm,
+                      cudaStream_t stream);
+
 // binning
 size_t bin_workspace_bytes(long long n_points, int n_polys);
 int launch_bin_count(const int2 *points, long long n_points, const int32_t *poly_offsets,

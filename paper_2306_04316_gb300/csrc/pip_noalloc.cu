@@ -98,6 +98,7 @@ extern "C" int pip_classify_noalloc(const int32_t *points, int64_t n_points, con
     a.out_bits = out_bits;
     a.words_per_poly = (n_points + 31) / 32;
     a.stats = nullptr;   // the statistics counters are allocated memory: not updated here
+    a.slab = nullptr;
     int err = launch_filtered(a, total_bits, current_tuning(), n_sm, ll, NOALLOC_CAP, s);
     if (err) { g_noalloc_cuda = err; return PIP_ERR_CUDA; }
     return PIP_OK;
