@@ -82,7 +82,8 @@ typedef struct pip_stats {
  * pip_classify -- the filtered batched kernels (Method, steps 2-7; Constraint 1).
  * Each polygon is rebased to a local frame at the centre of its bounding box.  When the box
  * is small (width, height < 2^30, width x height < 2^30) every pair test is exact in 32-bit
- * integer arithmetic; otherwise the side test (p - R_i) . n runs in FP32 with a proven
+ * integer arithmetic; when it is below 2^31 on both sides, exact with 64-bit products of
+ * 32-bit differences; otherwise the side test (p - R_i) . n runs in FP32 with a proven
  * forward-error bound, and any candidate with a (point, edge) pair whose FP32 value lies
  * within the bound is re-tested exactly with 64/128-bit integers.  The result is exact
  * either way.  Polygons of up to 256 vertices run in a kernel where each warp takes runs of

@@ -1,5 +1,5 @@
-// Filtered classification (pip_classify): exact int32 tests for compact polygons, an FP32
-// filter with an exact integer recheck for the rest.
+// Filtered classification (pip_classify): exact int32 or int64 tests for polygons whose box is
+// below 2^31, an FP32 filter with an exact integer recheck for the rest.
 //
 // Method section, steps 2-7 with Constraint 1.  For the edge R_i -> R_j of a polygon and a
 // candidate point p, the crossing counts when the straddle test (y_i > p_y) != (y_j > p_y)
@@ -31,6 +31,13 @@
 // magnitude, so the same record evaluated with wrapping 32-bit integer multiply-adds gives
 // -sign(d_y) det exactly; the straddle test is the sign bit of (P_y - Y_j) XOR (P_y - Y_i).
 // No filter and no recheck are needed for such polygons (building footprints, parcels).
+//
+// Exact int64 evaluation.  When the box is below 2^31 on both sides but too large for int32,
+// the record (X_i, Y_i, s d_x, d_y) holds int32 values in the box-centre frame and
+// nt = (P_x - X_i)|d_y| + (Y_i - P_y) s d_x = -s det is formed exactly from two 32 x 32 -> 64-bit
+// products (every factor below 2^31): again no filter and no recheck.  A run with any polygon
+// outside the int32 test puts all its polygons on the int64 or FP32 test, so the lanes of a
+// round walk at most two kinds of loop.  Only boxes of 2^31 or more use the FP32 filter.
 //
 // Two kernels, launched back to back on the caller's stream:
 //
@@ -121,9 +128,10 @@ constexpr int WP_R = 8;             // candidate rounds of 32 per run
 constexpr int WP_C = 32 * WP_R;     // candidates of a run
 constexpr long long LARGE_W = 1LL << 18;   // (candidates x vertices) above which a polygon is large
 // Arithmetic of a polygon's pair tests: exact int32 when its box is small enough that every
-// value fits (width, height < 2^30 and width * height < 2^30), else the FP32 filter, with
-// int64/double records when the box is 2^30 or more from its centre.
-constexpr int MODE_INT32 = 0, MODE_FP32 = 1, MODE_WIDE = 2;
+// value fits (width, height < 2^30 and width * height < 2^30); exact int64 products of int32
+// differences when the box is below 2^31 on both sides; else the FP32 filter, with int64/double
+// records when the box is 2^30 or more from its centre.
+constexpr int MODE_INT32 = 0, MODE_INT64 = 1, MODE_FP32 = 2, MODE_WIDE = 3;
 
 // A polygon goes to k_pip_large when it has more vertices than a run holds or more
 // (candidate, edge) pairs than one warp should walk.
@@ -133,13 +141,14 @@ __device__ __forceinline__ bool is_large_polygon(long long m, long long n)
 }
 
 struct __align__(16) WarpSmem {
-    float4 rec[WP_V];               // edge records of the run (int32 or FP32, per polygon)
+    float4 rec[WP_V];               // edge records of the run (int32, int64 or FP32, per polygon)
     int2 v[WP_V];                   // the run's vertices
     int4 box[32];                   // per chunk polygon: closed bounding box
     int4 fr[32];                    // ox, oy, bound (float bits), e0 | e1 << 9 | mode << 18
     int2 pt[WP_C];                  // candidate points of the slice
     unsigned vstart[WP_V / 32 + 1]; // bit i: vertex i starts a polygon of the run, or i == nv
     unsigned char sp[WP_C];         // first candidate slot of a polygon -> chunk polygon
+    unsigned char vp[WP_V];         // vertex -> chunk polygon
 };
 
 // Sets exactly the bits `mask` of *word to `bits` (other bits untouched, no zero-fill needed).
@@ -290,6 +299,7 @@ __global__ void __launch_bounds__(WP_THREADS, WP_CTAS) k_pip_warp(ClassifyArgs a
             if (mine && pe > pb) atomicOr(&S.vstart[(pb - vb) >> 5], 1u << ((pb - vb) & 31));
             if (lane == 0) atomicOr(&S.vstart[nv >> 5], 1u << (nv & 31));
             bool staged = false;
+            bool run_all32 = true;   // every polygon of the run takes the int32 test
 
             for (CI c0 = cbp; c0 < cq; c0 += WP_C) {
                 const int nc = (int)min((CI)WP_C, cq - c0);
@@ -351,8 +361,10 @@ __global__ void __launch_bounds__(WP_THREADS, WP_CTAS) k_pip_warp(ClassifyArgs a
                     __syncwarp();
                     // ---- per polygon (lane per polygon): box, arithmetic mode, closing edge; all of
                     //      its records in FP32 when the box is too large for the int32 test
+                    int mode = MODE_INT32;
+                    int4 fr4 = make_int4(0, 0, 0, 0), box4 = make_int4(0, 0, 0, 0);
+                    const int e0 = pb - vb, e1 = pe - vb;
                     if (mine) {
-                        const int e0 = pb - vb, e1 = pe - vb;
                         int x0 = INT_MAX, y0 = INT_MAX, x1 = INT_MIN, y1 = INT_MIN;
                         #pragma unroll 2
                         for (int i = e0; i < e1; ++i) {
@@ -361,26 +373,51 @@ __global__ void __launch_bounds__(WP_THREADS, WP_CTAS) k_pip_warp(ClassifyArgs a
                         }
                         const unsigned W = (unsigned)x1 - (unsigned)x0, H = (unsigned)y1 - (unsigned)y0;
                         const unsigned Mx = W - (W >> 1), My = H - (H >> 1);
-                        const int ox = x0 + (int)(W >> 1), oy = y0 + (int)(H >> 1);
-                        int mode = MODE_INT32, bound = 0;
+                        int bound = 0;
                         if (!(W < (1u << 30) && H < (1u << 30) && (unsigned long long)W * H < (1ULL << 30))) {
-                            mode = (Mx >= (1u << 30)) | (My >= (1u << 30)) ? MODE_WIDE : MODE_FP32;
-                            bound = __float_as_int(
-                                __fmul_ru(PM_BOUND_K, __fadd_ru(__fmul_ru(__uint2float_ru(Mx), __uint2float_ru(H)),
-                                                                __fmul_ru(__uint2float_ru(My), __uint2float_ru(W)))));
-                        }
-                        S.fr[lane] = make_int4(ox, oy, bound, e0 | (e1 << 9) | (mode << 18));
-                        S.box[lane] = make_int4(x0, y0, x1, y1);
-                        if (e1 > e0) {
-                            if (mode == MODE_INT32) {
-                                const int4 r4 = int32_record(S.v[e1 - 1], S.v[e0]);
-                                S.rec[e1 - 1] = make_float4(__int_as_float(r4.x), __int_as_float(r4.y),
-                                                            __int_as_float(r4.z), __int_as_float(r4.w));
+                            if (W < (1u << 31) && H < (1u << 31)) {
+                                mode = MODE_INT64;
                             } else {
-                                for (int i = e0; i < e1; ++i) {
-                                    const int2 ri = S.v[i], rj = S.v[i + 1 == e1 ? e0 : i + 1];
-                                    S.rec[i] = mode == MODE_FP32 ? fp32_record(ri, rj, ox, oy) : wide_record(ri, rj, ox, oy);
-                                }
+                                mode = (Mx >= (1u << 30)) | (My >= (1u << 30)) ? MODE_WIDE : MODE_FP32;
+                                bound = __float_as_int(__fmul_ru(
+                                    PM_BOUND_K, __fadd_ru(__fmul_ru(__uint2float_ru(Mx), __uint2float_ru(H)),
+                                                          __fmul_ru(__uint2float_ru(My), __uint2float_ru(W)))));
+                            }
+                        }
+                        fr4 = make_int4(x0 + (int)(W >> 1), y0 + (int)(H >> 1), bound, e0 | (e1 << 9));
+                        box4 = make_int4(x0, y0, x1, y1);
+                    }
+                    // a run with any polygon outside the int32 test puts its int32 polygons on the
+                    // int64 test too, so that a round walks at most two kinds of loop
+                    run_all32 = __all_sync(FULL, mode == MODE_INT32);
+                    if (!run_all32 && mode == MODE_INT32) mode = MODE_INT64;
+                    if (mine) {
+                        S.fr[lane] = make_int4(fr4.x, fr4.y, fr4.z, fr4.w | (mode << 18));
+                        S.box[lane] = box4;
+                        if (mode == MODE_INT32 && e1 > e0) {
+                            const int4 r4 = int32_record(S.v[e1 - 1], S.v[e0]);
+                            S.rec[e1 - 1] = make_float4(__int_as_float(r4.x), __int_as_float(r4.y),
+                                                        __int_as_float(r4.z), __int_as_float(r4.w));
+                        }
+                        if (!run_all32)
+                            for (int i = e0; i < e1; ++i) S.vp[i] = (unsigned char)lane;
+                    }
+                    __syncwarp();
+                    if (!run_all32) {
+                        // int64 / FP32 / wide records, lane per edge, in each polygon's frame
+                        for (int i = lane; i < nv; i += 32) {
+                            const int4 f = S.fr[S.vp[i]];
+                            const int e0 = f.w & 0x1ff, e1 = (f.w >> 9) & 0x1ff, md = f.w >> 18;
+                            const int2 ri = S.v[i], rj = S.v[i + 1 == e1 ? e0 : i + 1];
+                            if (md == MODE_INT64) {
+                                // (X_i, Y_i, s d_x, d_y), s = sign(d_y); every value below 2^31
+                                const int dx = rj.x - ri.x, dy = rj.y - ri.y;
+                                reinterpret_cast<int4 *>(S.rec)[i] =
+                                    make_int4(ri.x - f.x, ri.y - f.y, dy > 0 ? dx : -dx, dy);
+                            } else if (md == MODE_FP32) {
+                                S.rec[i] = fp32_record(ri, rj, f.x, f.y);
+                            } else {
+                                S.rec[i] = wide_record(ri, rj, f.x, f.y);
                             }
                         }
                     }
@@ -436,44 +473,71 @@ __global__ void __launch_bounds__(WP_THREADS, WP_CTAS) k_pip_warp(ClassifyArgs a
                             acc ^= (u ^ up) & nt;
                             up = u;
                         }
-                        parity = (int)(acc >> 31);
+                        if (gi) parity = (int)(acc >> 31);
                     }
-                    const bool gf = go && mode != MODE_INT32;
-                    const int kf = __reduce_max_sync(FULL, gf ? e1 - e0 : 0);
-                    if (kf > 0) {
-                        unsigned ad = rec_base + 16u * (unsigned)(gf ? e0 : 0);
-                        const unsigned al = rec_base + 16u * (unsigned)(gf ? e1 - 1 : 0);
-                        const int py = p2.y;
-                        const float B = __int_as_float(f.z);
-                        const float Px = __ll2float_rn((long long)p2.x - f.x);
-                        const float Py = __ll2float_rn((long long)p2.y - f.y);
-                        bool sp = lds128(al).w > py;   // vertex e0
-                        bool unc = false;
-                        int par = 0;
-                        #pragma unroll 2
-                        for (int k = 0; k < kf; ++k) {
-                            const unsigned acur = ad;
-                            const int4 q4 = lds128(ad);
-                            ad = __viaddmin_u32(ad, 16u, al);
-                            const bool sn = q4.w > py;
-                            const bool st = sn != sp;
-                            sp = sn;
-                            float tt = __fmaf_rn(-Px, __int_as_float(q4.y), __int_as_float(q4.x));
-                            tt = __fmaf_rn(Py, __int_as_float(q4.z), tt);
-                            if (VERIFY && gf && st && !(fabsf(tt) <= B)) {   // a trusted FP32 sign
-                                const int e = (int)((acur - rec_base) >> 4);
-                                const int2 ri = S.v[e], rj = S.v[e + 1 == e1 ? e0 : e + 1];
-                                st_err += exact_edge_counts(p2.x, p2.y, ri.x, ri.y, rj.x, rj.y) != (int)(tt > 0.f);
-                                ++st_ver;
+                    if (!run_all32) {
+                        const bool g6 = go && mode == MODE_INT64;
+                        const int k6 = __reduce_max_sync(FULL, g6 ? e1 - e0 : 0);
+                        if (k6 > 0) {
+                            // record (X_i, Y_i, s d_x, d_y) in the frame; u = P_y - y: the straddle test is
+                            // the sign bit of u_i ^ u_j, and nt = (P_x - X_i)|d_y| + (Y_i - P_y) s d_x =
+                            // -s det in int64 (every factor below 2^31); a crossing counts when the
+                            // straddle bit and nt's sign bit are both set
+                            unsigned ad = rec_base + 16u * (unsigned)(g6 ? e0 : 0);
+                            const unsigned al = rec_base + 16u * (unsigned)(g6 ? e1 - 1 : 0);
+                            const unsigned Px = (unsigned)p2.x - (unsigned)f.x, Py = (unsigned)p2.y - (unsigned)f.y;
+                            unsigned up = Py - (unsigned)lds128(ad).y;   // vertex e0
+                            unsigned acc = 0;
+                            #pragma unroll 2
+                            for (int k = 0; k < k6; ++k) {
+                                const int4 q4 = lds128(ad);
+                                ad = __viaddmin_u32(ad, 16u, al);
+                                const unsigned ui = Py - (unsigned)q4.y;              // P_y - Y_i
+                                const unsigned uj = ui - (unsigned)q4.w;              // P_y - Y_j
+                                const long long nt = (long long)(int)(Px - (unsigned)q4.x) * (long long)abs(q4.w) -
+                                                     (long long)(int)ui * (long long)q4.z;
+                                acc ^= (up ^ uj) & (unsigned)((unsigned long long)nt >> 32);
+                                up = uj;
                             }
-                            par ^= (int)(st & (tt > 0.f));
-                            unc |= st & (fabsf(tt) <= B);
+                            if (g6) parity = (int)(acc >> 31);
                         }
-                        if (gf) {
-                            parity = par;
-                            if (unc) {
-                                ++st_fbp;
-                                parity = exact_parity(S.v, e0, e1, true, p2);
+                        const bool gf = go && mode >= MODE_FP32;
+                        const int kf = __reduce_max_sync(FULL, gf ? e1 - e0 : 0);
+                        if (kf > 0) {
+                            unsigned ad = rec_base + 16u * (unsigned)(gf ? e0 : 0);
+                            const unsigned al = rec_base + 16u * (unsigned)(gf ? e1 - 1 : 0);
+                            const int py = p2.y;
+                            const float B = __int_as_float(f.z);
+                            const float Px = __ll2float_rn((long long)p2.x - f.x);
+                            const float Py = __ll2float_rn((long long)p2.y - f.y);
+                            bool sp = lds128(al).w > py;   // vertex e0
+                            bool unc = false;
+                            int par = 0;
+                            #pragma unroll 2
+                            for (int k = 0; k < kf; ++k) {
+                                const unsigned acur = ad;
+                                const int4 q4 = lds128(ad);
+                                ad = __viaddmin_u32(ad, 16u, al);
+                                const bool sn = q4.w > py;
+                                const bool st = sn != sp;
+                                sp = sn;
+                                float tt = __fmaf_rn(-Px, __int_as_float(q4.y), __int_as_float(q4.x));
+                                tt = __fmaf_rn(Py, __int_as_float(q4.z), tt);
+                                if (VERIFY && gf && st && !(fabsf(tt) <= B)) {   // a trusted FP32 sign
+                                    const int e = (int)((acur - rec_base) >> 4);
+                                    const int2 ri = S.v[e], rj = S.v[e + 1 == e1 ? e0 : e + 1];
+                                    st_err += exact_edge_counts(p2.x, p2.y, ri.x, ri.y, rj.x, rj.y) != (int)(tt > 0.f);
+                                    ++st_ver;
+                                }
+                                par ^= (int)(st & (tt > 0.f));
+                                unc |= st & (fabsf(tt) <= B);
+                            }
+                            if (gf) {
+                                parity = par;
+                                if (unc) {
+                                    ++st_fbp;
+                                    parity = exact_parity(S.v, e0, e1, true, p2);
+                                }
                             }
                         }
                     }
