@@ -409,3 +409,61 @@ def test_paper_rules_match_the_oracle(api, algorithm):
         got = out.cpu().numpy().view(np.uint32)[:w.n_words]
         want = oracle.classify_rule(w.points, w.poly_offsets, w.verts, algorithm, w.cand_offsets, w.cand_ids)
         assert_same(got, want, w.n_bits, f"{w.name} algorithm {algorithm}")
+
+
+# ------------------------------------------------------------------------------------------
+# CUDA-graph capture and replay (binning + classification)
+# ------------------------------------------------------------------------------------------
+
+def test_graph_replay_of_binning_and_classification(api):
+    """One captured graph bins a batch of points and classifies it; replaying it after new
+    points are copied into the same buffer gives each batch's oracle bits."""
+    clusters, po, v = W.join_polygons(seed=2306043160 + 90, n_polys=2000)
+    batches = [W.join_points(clusters, 2306043160 + 91 + b, 200_000) for b in range(3)]
+    d_po, d_v = torch.from_numpy(po).cuda(), torch.from_numpy(v).cuda()
+    d_pts = torch.from_numpy(batches[0]).cuda()
+    P, n = len(po) - 1, len(batches[0])
+    stream = torch.cuda.Stream()
+    ws = api.bin_workspace(n, P)
+    co = torch.empty(P + 1, dtype=torch.int32, device="cuda")
+    tot = torch.empty(1, dtype=torch.int64, device="cuda")
+    cap = 4 * n
+    ids = torch.empty(cap, dtype=torch.int32, device="cuda")
+    out = torch.empty(cap // 32 + 1, dtype=torch.int32, device="cuda")
+    ovf = torch.zeros(1, dtype=torch.int32, device="cuda")
+
+    def step():
+        api.pip_bin_count(d_pts, d_po, d_v, workspace=ws, cand_offsets=co, d_total=tot, stream=stream)
+        api.pip_bin_fill(d_pts, d_po, d_v, ws, co, ids, d_overflow=ovf, stream=stream)
+        api.pip_classify(d_pts, d_po, d_v, co, ids, out=out, stream=stream)
+
+    with torch.cuda.stream(stream):
+        step()                                   # first call on the stream: allocates its list
+    stream.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=stream):
+        step()
+    for b in batches:
+        d_pts.copy_(torch.from_numpy(b))
+        torch.cuda.synchronize()
+        with torch.cuda.stream(stream):
+            g.replay()
+        stream.synchronize()
+        assert int(ovf.item()) == 0
+        n_c = int(tot.item())
+        c_host = co.cpu().numpy().astype(np.int64)
+        i_host = ids[:n_c].cpu().numpy()
+        got = out.cpu().numpy().view(np.uint32)[:(n_c + 31) // 32]
+        # candidate sets against the oracle's closed-box join; the bits against the oracle's
+        # classification of its own candidate lists, matched by (polygon, point id)
+        counts, want_ids = oracle.bbox_join(b, po, v, np.arange(P))
+        assert np.array_equal(np.diff(c_host), counts)
+        owner = np.repeat(np.arange(P), counts)
+        perm = np.lexsort((i_host, owner))           # GPU positions in (polygon, id) order
+        assert np.array_equal(i_host[perm], want_ids)
+        oco = np.zeros(P + 1, dtype=np.int64)
+        oco[1:] = np.cumsum(counts)
+        want_bits = oracle.unpack_bits(oracle.classify(b, po, v, oco, want_ids), n_c)
+        got_bits = oracle.unpack_bits(got, n_c)[perm]
+        bad = np.nonzero(got_bits != want_bits)[0]
+        assert len(bad) == 0, f"graph replay: {len(bad)} of {n_c} bits differ"
