@@ -189,6 +189,19 @@ int pip_classify_noalloc(const int32_t *points, int64_t n_points,
                          uint32_t *out_bits, void *stream);
 
 /*
+ * pip_quantize_lonlat -- float64 coordinates to the int32 fixed point every other call takes
+ * (not in the paper, which computes on float64 lon/lat; the step upstream of the hot path).
+ * out[i] = rint(lonlat[i] * scale): the product rounded once in IEEE float64, then rounded to
+ * the nearest integer with ties to even.  scale = 1e7 gives 1e-7-degree units.  lonlat and out
+ * are device arrays of n_values values (interleaved x, y for points or vertices: n_values = 2 *
+ * count).  A value that is NaN, infinite or outside int32 after rounding is written as 0 and
+ * ORs a bit into *d_status (device int32, may be NULL; 1 = NaN, 2 = out of range), which the
+ * caller zeroes first.  Returns PIP_OK, PIP_ERR_INVALID (scale not positive) or PIP_ERR_*.
+ */
+int pip_quantize_lonlat(const double *lonlat, int64_t n_values, double scale, int32_t *out,
+                        int32_t *d_status, void *stream);
+
+/*
  * Uniform-grid binning (not in the paper; it builds the candidate CSR of a spatial join):
  * candidates of polygon k = every point inside k's CLOSED bounding box, listed in a fixed
  * order (grid cells row-major over the box, ascending point id within a cell), so that

@@ -134,6 +134,20 @@ def classify_rule(points, poly_offsets, verts, rule, cand_offsets=None, cand_ids
     return out
 
 
+def quantize(values, scale=1e7):
+    """float64 -> int32 fixed point by the plain definition: rint(v * scale) with the product
+    rounded once in float64 and ties to even; (out, status) with status bit 1 for NaN and bit 2
+    for a result outside int32 (those values become 0)."""
+    v = np.asarray(values, dtype=np.float64)
+    with np.errstate(invalid="ignore", over="ignore"):
+        q = np.rint(v * np.float64(scale))
+    nan = np.isnan(q)
+    out_of_range = ~nan & ((q < -2.0**31) | (q > 2.0**31 - 1))
+    out = np.where(nan | out_of_range, 0, np.nan_to_num(q)).astype(np.int64).astype(np.int32)
+    status = (1 if nan.any() else 0) | (2 if out_of_range.any() else 0)
+    return out, status
+
+
 def classify_sample(points, poly_offsets, verts, sample, cand_offsets=None, cand_ids=None):
     """0/1 per listed bit index (candidate index, or k*32*W + j in dense mode)."""
     lib = _load()

@@ -57,6 +57,7 @@ _SIGS = {
     "pip_classify_paper": ([_P, _I64, _P, _P, _I32, _P, _P, _I32, _P, _P], ctypes.c_int),
     "pip_classify_slab": ([_P, _I64, _P, _P, _I32, _P, _P, _P, _P, _P], ctypes.c_int),
     "pip_slab_index_bytes": ([_I32, _I64, _I32, _I64], ctypes.c_size_t),
+    "pip_quantize_lonlat": ([_P, _I64, ctypes.c_double, _P, _P, _P], ctypes.c_int),
     "pip_slab_build": ([_P, _P, _I32, _I64, _I32, _P, ctypes.c_size_t, _P, _P], ctypes.c_int),
     "pip_bin_workspace_bytes": ([_I64, _I32], ctypes.c_size_t),
     "pip_bin_count": ([_P, _I64, _P, _P, _I32, _I32, _P, ctypes.c_size_t, _P, _P, _P], ctypes.c_int),

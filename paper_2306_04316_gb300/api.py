@@ -14,7 +14,7 @@ import torch
 
 from . import _lib
 
-__all__ = ["pip_classify", "pip_classify_exact", "pip_classify_paper", "pip_classify_slab", "slab_index", "pip_classify_noalloc", "pip_bin_count", "pip_bin_fill", "bin_join",
+__all__ = ["pip_classify", "pip_classify_exact", "pip_classify_paper", "pip_classify_slab", "slab_index", "quantize_lonlat", "pip_classify_noalloc", "pip_bin_count", "pip_bin_fill", "bin_join",
            "pip_set_tuning", "pip_get_tuning", "pip_get_stats", "pip_reset_stats", "pip_launch_count", "pip_set_verify", "pip_validate",
            "out_words", "to_device"]
 
@@ -96,6 +96,19 @@ def pip_classify_paper(points, poly_offsets, verts, cand_offsets=None, cand_ids=
     """The paper's Algorithm 1 or 2 evaluated literally (``pip_classify_paper``)."""
     return _classify("pip_classify_paper", points, poly_offsets, verts, cand_offsets, cand_ids, out,
                      n_cands, stream, extra=(int(algorithm),))
+
+
+def quantize_lonlat(lonlat, scale=1e7, out=None, stream=None):
+    """float64 lon/lat (CUDA tensor, any shape) -> int32 fixed point (``pip_quantize_lonlat``);
+    returns (out, status) with status a one-element int32 tensor (0 = every value converted)."""
+    if not (lonlat.is_cuda and lonlat.dtype == torch.float64 and lonlat.is_contiguous()):
+        raise ValueError("lonlat must be a contiguous float64 CUDA tensor")
+    if out is None:
+        out = torch.empty(lonlat.shape, dtype=torch.int32, device=lonlat.device)
+    status = torch.zeros(1, dtype=torch.int32, device=lonlat.device)
+    _lib.check("pip_quantize_lonlat", _lib.load().pip_quantize_lonlat(_ptr(lonlat), lonlat.numel(), float(scale),
+                                                                       _ptr(out), _ptr(status), _stream(stream)))
+    return out, status
 
 
 def slab_index(poly_offsets, verts, edges_per_slab=8, stream=None):

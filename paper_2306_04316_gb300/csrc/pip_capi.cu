@@ -174,6 +174,22 @@ int pip_classify_slab(const int32_t *points, int64_t n_points, const int32_t *po
     return e == 0 ? PIP_OK : cuda_fail((cudaError_t)e);
 }
 
+int pip_quantize_lonlat(const double *lonlat, int64_t n_values, double scale, int32_t *out, int32_t *d_status,
+                        void *stream)
+{
+    if (n_values < 0) return PIP_ERR_SIZE;
+    if (!(scale > 0.0) || scale != scale) return PIP_ERR_INVALID;
+    if (n_values > 0 && (!lonlat || !out)) return PIP_ERR_NULL;
+    if (misaligned(lonlat, 8) || misaligned(out, 4) || misaligned(d_status, 4)) return PIP_ERR_ALIGN;
+    if (n_values == 0) return PIP_OK;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    DeviceState *ds = nullptr;
+    int rc = device_state(s, &ds);
+    if (rc != PIP_OK) return rc;
+    int e = launch_quantize(lonlat, n_values, scale, out, d_status, ds->n_sm, s);
+    return e == 0 ? PIP_OK : cuda_fail((cudaError_t)e);
+}
+
 size_t pip_slab_index_bytes(int32_t n_polys, int64_t n_verts, int32_t edges_per_slab, int64_t capacity)
 {
     if (n_polys < 0 || n_verts < 0 || edges_per_slab < 1 || edges_per_slab > 256 || capacity < 0) return 0;

@@ -40,6 +40,10 @@ int launch_slab_build(const int32_t *poly_offsets, const int2 *verts, int n_poly
                       int edges_per_slab, void *index, size_t index_bytes, long long *d_entries, int n_sm,
                       cudaStream_t stream);
 
+// quantisation of float64 lon/lat
+int launch_quantize(const double *v, long long n, double scale, int32_t *out, int *status, int n_sm,
+                    cudaStream_t stream);
+
 // binning
 size_t bin_workspace_bytes(long long n_points, int n_polys);
 int launch_bin_count(const int2 *points, long long n_points, const int32_t *poly_offsets,
