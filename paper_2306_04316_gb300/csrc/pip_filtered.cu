@@ -58,10 +58,12 @@
 // k_pip_large -- the listed polygons.  Work items (polygon, block of 256*PPT candidates,
 //   slice of edges) are taken from the list by atomic counters; the CTA streams the slice
 //   through shared memory in tiles of T edges, each tile framed by the union of its vertices
-//   and the block's candidate points, and XORs the partial parities into the output words
-//   (stream order puts it after the first kernel's writes).  Its last CTA empties the list for
-//   the next call.  With more large polygons than the list holds, it falls back to a scan over
-//   all polygons.
+//   and the block's candidate points (records scaled per edge by a power of two, so that one
+//   uniform test flags the uncertain FP32 signs), and XORs the partial parities into the output
+//   words (stream order puts it after the first kernel's writes).  With a y-slab index
+//   (pip_classify_slab) an item is a candidate block whose points walk only their slab's edges.
+//   Its last CTA empties the list for the next call.  With more large polygons than the list
+//   holds, it falls back to a scan over all polygons.
 #include <algorithm>
 #include <type_traits>
 
@@ -69,7 +71,6 @@
 #include "pip_launch.h"
 
 namespace pipdev {
-
 
 // large-polygon kernel geometry
 constexpr int LG_THREADS = 256;
@@ -87,8 +88,6 @@ __device__ __forceinline__ float edge_c(int2 ri, long long dx, long long dy, int
     return dy > 0 ? c : -c;
 }
 
-
-
 // Edge record of a frame 2^30 or more wide (int64 and double arithmetic; rare, out of line).
 __device__ __noinline__ float4 wide_record(int2 ri, int2 rj, int ox, int oy)
 {
@@ -97,7 +96,6 @@ __device__ __noinline__ float4 wide_record(int2 ri, int2 rj, int ox, int oy)
     return dy > 0 ? make_float4(c, __ll2float_rn(dy), __ll2float_rn(dx), __int_as_float(rj.y))
                   : make_float4(c, __ll2float_rn(-dy), __ll2float_rn(-dx), __int_as_float(rj.y));
 }
-
 
 // Exact parity of p over the edges e0..e1-1 of staged vertices v, edge e running from v[e]
 // to v[e + 1], or to v[e0] for the last edge when `wrap`.  Rare path: kept out of line.
@@ -122,10 +120,10 @@ __device__ __noinline__ int exact_parity(const int2 *v, int e0, int e1, bool wra
 // the polygon's height and width (>= |d_y|, |d_x| of every edge).
 constexpr float PM_BOUND_K = 7.748603820800781e-07f;     // 13 * 2^-24 (exact in FP32)
 constexpr int WP_THREADS = 128;     // 4 independent warps per CTA
-constexpr int WP_CTAS = 5;          // CTAs per SM (shared memory: 4 x 9.3 KB per CTA)
+constexpr int WP_CTAS = 5;          // CTAs per SM (shared memory: 4 x 9.8 KB per CTA)
 constexpr int WP_V = 256;           // vertices of a run (and most vertices of a small polygon)
-constexpr int WP_R = 8;             // candidate rounds of 32 per run
-constexpr int WP_C = 32 * WP_R;     // candidates of a run
+constexpr int WP_R = 8;             // candidate rounds of 32 per slice
+constexpr int WP_C = 32 * WP_R;     // candidates of a slice
 constexpr long long LARGE_W = 1LL << 18;   // (candidates x vertices) above which a polygon is large
 // Arithmetic of a polygon's pair tests: exact int32 when its box is small enough that every
 // value fits (width, height < 2^30 and width * height < 2^30); exact int64 products of int32
