@@ -100,3 +100,36 @@ def test_bin_workspace_size_grows(lib):
     b = lib.pip_bin_workspace_bytes(10_000_000, 100_000)
     assert 0 < a < b
     assert b >= 10_000_000 * (4 * 4 + 8)
+
+
+def test_argument_checks_of_the_other_entry_points(lib):
+    from paper_2306_04316_gb300 import _lib
+    P = ctypes.c_void_p
+    a8 = P(0x1000)
+    a256 = P(0x10000)
+    # the printed-algorithm rules: only 1 and 2
+    for alg in (0, 3, -1):
+        assert lib.pip_classify_paper(a8, 4, a8, a8, 1, None, None, alg, a8, None) == _lib.PIP_ERR_INVALID
+    assert lib.pip_classify_paper(a8, -1, a8, a8, 1, None, None, 1, a8, None) == _lib.PIP_ERR_SIZE
+    # slab index: edges per slab 1..256, 256-byte aligned buffer, a buffer at least its fixed part
+    assert lib.pip_slab_index_bytes(10, 1000, 0, 0) == 0
+    assert lib.pip_slab_index_bytes(10, 1000, 257, 0) == 0
+    assert lib.pip_slab_index_bytes(-1, 1000, 8, 0) == 0
+    fixed = lib.pip_slab_index_bytes(10, 1000, 8, 0)
+    assert 0 < fixed < lib.pip_slab_index_bytes(10, 1000, 8, 5000)
+    assert lib.pip_slab_build(a8, a8, 10, 1000, 0, a256, fixed, None, None) == _lib.PIP_ERR_INVALID
+    assert lib.pip_slab_build(a8, a8, 10, 1000, 8, P(0x10010), fixed, None, None) == _lib.PIP_ERR_ALIGN
+    assert lib.pip_slab_build(a8, a8, 10, 1000, 8, a256, fixed - 1, None, None) == _lib.PIP_ERR_WORKSPACE
+    assert lib.pip_slab_build(a8, a8, 10, -1, 8, a256, fixed, None, None) == _lib.PIP_ERR_SIZE
+    assert lib.pip_slab_build(None, a8, 10, 1000, 8, a256, fixed, None, None) == _lib.PIP_ERR_NULL
+    assert lib.pip_classify_slab(a8, 4, a8, a8, 1, None, None, P(0x10010), a8, None) == _lib.PIP_ERR_ALIGN
+    # quantisation: positive scale, aligned arrays
+    assert lib.pip_quantize_lonlat(a8, 4, 0.0, a8, None, None) == _lib.PIP_ERR_INVALID
+    assert lib.pip_quantize_lonlat(a8, 4, float("nan"), a8, None, None) == _lib.PIP_ERR_INVALID
+    assert lib.pip_quantize_lonlat(a8, -1, 1e7, a8, None, None) == _lib.PIP_ERR_SIZE
+    assert lib.pip_quantize_lonlat(P(0x1004), 4, 1e7, a8, None, None) == _lib.PIP_ERR_ALIGN
+    assert lib.pip_quantize_lonlat(None, 4, 1e7, a8, None, None) == _lib.PIP_ERR_NULL
+    assert lib.pip_quantize_lonlat(None, 0, 1e7, None, None, None) == _lib.PIP_OK
+    # verification mode: 0 or 1
+    assert lib.pip_set_verify(2) == _lib.PIP_ERR_INVALID
+    assert lib.pip_set_verify(0) == _lib.PIP_OK
