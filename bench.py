@@ -331,6 +331,10 @@ def run_join(args, rank, world):
         one_pass()
     stream.synchronize()
     assert int(ovf.sum().item()) == 0
+    # the large-polygon kernel's tuning, picked by the autotuner on the first batch
+    from paper_2306_04316_gb300 import tuning
+    best, times = tuning.autotune(d_pts[0], d_po, d_v, co[0], ids[0], n_cands=totals[0], cache=False)
+    autotuned = {"best": list(best), "candidates": len(times), "best_ms": times[best]}
     m = np.diff(po.astype(np.int64))
     T = sum(int((m * np.diff(c.cpu().numpy().astype(np.int64))).sum()) for c in co)
     C = sum(int(c[-1].item()) for c in co)
@@ -391,7 +395,8 @@ def run_join(args, rank, world):
                 "config": {"workload": f"join: {P} polygons x {nb} batches of {n_pts} clustered points, "
                                        f"{C} candidates from GPU binning, one CUDA-graph replay per step",
                            "pair_tests_per_step": T, "candidates_per_step": C, "binning_ms_per_step": bin_ms,
-                           "classify_ms_per_step": ms - bin_ms, "l2": "inputs larger than L2 (no flush)"},
+                           "classify_ms_per_step": ms - bin_ms, "tuning": list(api.pip_get_tuning()),
+                           "autotuned": autotuned, "l2": "inputs larger than L2 (no flush)"},
                 "points_per_s": job_rate(nb * n_pts * world, ms), "cpu_baseline": cpu, "clocks": clocks,
                 "gpu_launches": per_replay["full"] * args.steps,
                 "roofline": {"bound": "hbm", "achieved": join_bytes / (ms / 1000.0) / 1e9, "peak": hbm,
@@ -427,6 +432,9 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--batches", type=int, default=20, help="join workload: point batches per step")
     ap.add_argument("--tuning", default="", help="edge_tile,pts_per_thread,ctas_per_sm (0 = keep)")
+    ap.add_argument("--autotune", action="store_true",
+                    help="pick the large-polygon kernel's tuning with the autotuner before timing "
+                         "(always on for --workload join)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -454,6 +462,12 @@ def main():
     d = api.to_device(w)
     n_words = w.n_words
     out = torch.empty(n_words, dtype=torch.int32, device="cuda")
+    autotuned = None
+    if args.autotune and args.kernel == "filtered":
+        from paper_2306_04316_gb300 import tuning
+        best, times = tuning.autotune(d["points"], d["poly_offsets"], d["verts"], d.get("cand_offsets"),
+                                      d.get("cand_ids"), n_cands=None if w.dense else w.n_bits, cache=False)
+        autotuned = {"best": list(best), "candidates": len(times), "best_ms": times[best]}
     fn = api.pip_classify if args.kernel == "filtered" else api.pip_classify_exact
     if args.semantics != "halfopen":
         algorithm = 1 if args.semantics == "alg1" else 2
@@ -602,7 +616,8 @@ def main():
             "config": {"workload": f"{w.name}: {w.n_polys} polygons, {w.n_candidates} candidates, "
                                    f"{w.verts.shape[0]} vertices", "pair_tests_per_step": T,
                        "algorithmic_bytes_per_step": B, "kernel": args.kernel,
-                       "tuning": list(api.pip_get_tuning()), "l2": "inputs larger than L2 (no flush)"},
+                       "tuning": list(api.pip_get_tuning()), "autotuned": autotuned,
+                       "l2": "inputs larger than L2 (no flush)"},
             "points_per_s": job_rate(C_all, ms_step),
             "roofline": roof,
             "cpu_baseline": cpu,
