@@ -423,6 +423,9 @@ def main():
                          "outside the timed region); changes the number of pair tests, so the line reports "
                          "points/s instead")
     ap.add_argument("--edges-per-slab", type=int, default=8)
+    ap.add_argument("--verify", action="store_true",
+                    help="after timing, one pass in verification mode: every trusted fast-path decision "
+                         "rechecked exactly; reports the disagreements (must be 0)")
     ap.add_argument("--semantics", default="halfopen", choices=["halfopen", "alg1", "alg2"],
                     help="alg1/alg2: time the paper's printed Algorithm 1 or 2 (pip_classify_paper) and "
                          "count the bits where it differs from the half-open rule")
@@ -596,6 +599,17 @@ def main():
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = oracle_baseline(w)
+    verification = None
+    if args.verify and args.kernel == "filtered" and args.semantics == "halfopen":
+        api.pip_set_verify(True)
+        try:
+            api.pip_reset_stats()
+            fn(d["points"], d["poly_offsets"], d["verts"], cand_o, cand_i, out=out)
+            torch.cuda.synchronize()
+            vs = api.pip_get_stats()
+        finally:
+            api.pip_set_verify(False)
+        verification = {"filter_errors": vs["filter_errors"], "verified_pairs": vs["verified_pairs"]}
     semantics = None
     if args.semantics != "halfopen":
         # bits where the paper's printed rule and the half-open rule disagree (not timed)
@@ -629,6 +643,8 @@ def main():
                              "value": (T / (other_ms / 1000.0)) if other_ms else None},
             "fallback_fraction": (stats["fallback_points"] / stats["candidates"]) if stats["candidates"] else None,
         }
+        if verification is not None:
+            line["verification"] = verification
         if index_info:
             line["metric"] = "points classified/s through a y-slab edge index (1 GB300), 0 mismatches"
             line["unit"] = "points/s"
