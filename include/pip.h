@@ -76,6 +76,8 @@ typedef struct pip_stats {
                                   error bound) differs from the exact 64/128-bit test; 0 means the
                                   filter was sound on every pair it trusted */
     uint64_t verified_pairs;   /* verification mode only: trusted decisions that were rechecked */
+    uint64_t wait_timeouts;    /* CTAs whose bounded wait for a bulk copy of edges gave up (their
+                                  bits are then unreliable; never expected, always 0 in tests) */
 } pip_stats;
 
 /*

@@ -30,7 +30,8 @@ class PipStats(ctypes.Structure):
                 ("fallback_points", ctypes.c_uint64),
                 ("exact_candidates", ctypes.c_uint64),
                 ("filter_errors", ctypes.c_uint64),
-                ("verified_pairs", ctypes.c_uint64)]
+                ("verified_pairs", ctypes.c_uint64),
+                ("wait_timeouts", ctypes.c_uint64)]
 
 
 class PipError(RuntimeError):

@@ -297,6 +297,7 @@ int pip_get_stats(pip_stats *out)
     out->exact_candidates = h[ST_EXACT_CANDIDATES];
     out->filter_errors = h[ST_FILTER_ERRORS];
     out->verified_pairs = h[ST_VERIFIED];
+    out->wait_timeouts = h[ST_WAIT_TIMEOUTS];
     return PIP_OK;
 }
 

@@ -25,6 +25,7 @@ enum StatIdx {
     ST_EXACT_CANDIDATES = 4,
     ST_FILTER_ERRORS = 5,     // verification mode: fast-path decisions that the exact test contradicts
     ST_VERIFIED = 6,          // verification mode: fast-path decisions checked
+    ST_WAIT_TIMEOUTS = 7,     // bounded waits on an asynchronous copy that gave up (never expected)
     ST_COUNT = 8
 };
 
@@ -42,6 +43,39 @@ struct LargeList {
 
 __device__ __forceinline__ int *large_entries(LargeList *l) { return reinterpret_cast<int *>(l + 1); }
 __device__ __forceinline__ int *large_taken(LargeList *l, int cap) { return reinterpret_cast<int *>(l + 1) + cap; }
+
+// One-dimensional bulk copy global -> shared through the tensor memory accelerator, completed on
+// an mbarrier (dst, src and bytes multiples of 16), and the barrier operations it needs.
+__device__ __forceinline__ void mbar_init(unsigned long long *bar, unsigned count)
+{
+    const unsigned a = (unsigned)__cvta_generic_to_shared(bar);
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(a), "r"(count) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+}
+__device__ __forceinline__ void bulk_copy_g2s(void *smem_dst, const void *gmem_src, unsigned bytes,
+                                              unsigned long long *bar)
+{
+    const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+    const unsigned b = (unsigned)__cvta_generic_to_shared(bar);
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(b), "r"(bytes) : "memory");
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n"
+                 ::"r"(d), "l"(gmem_src), "r"(bytes), "r"(b) : "memory");
+}
+// Waits for the barrier's phase `parity` to complete, giving up after `limit` polls; returns
+// whether it completed.
+__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned parity, int limit)
+{
+    const unsigned b = (unsigned)__cvta_generic_to_shared(bar);
+    for (int i = 0; i < limit; ++i) {
+        unsigned done;
+        asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                     "selp.u32 %0, 1, 0, p;\n\t}\n"
+                     : "=r"(done) : "r"(b), "r"(parity) : "memory");
+        if (done) return true;
+    }
+    return false;
+}
 
 // 8- and 4-byte asynchronous global -> shared copies (LDGSTS) and their group fences.
 __device__ __forceinline__ void cp_async8(void *smem_dst, const void *gmem_src)

@@ -57,7 +57,9 @@
 //
 // k_pip_large -- the listed polygons.  Work items (polygon, block of 256*PPT candidates,
 //   slice of edges) are taken from the list by atomic counters; the CTA streams the slice
-//   through shared memory in tiles of T edges, each tile framed by the union of its vertices
+//   through shared memory in tiles of T edges (each tile's vertices by one bulk copy of the
+//   tensor memory accelerator, completed on an mbarrier with a bounded wait), each tile framed
+//   by the union of its vertices
 //   and the block's candidate points (records scaled per edge by a power of two, so that one
 //   uniform test flags the uncertain FP32 signs), and XORs the partial parities into the output
 //   words (stream order puts it after the first kernel's writes).  With a y-slab index
@@ -582,8 +584,9 @@ __global__ void __launch_bounds__(WP_THREADS, WP_CTAS) k_pip_warp(ClassifyArgs a
 
 size_t filtered_smem_bytes(int T)
 {
-    // records float4[T], vertices int2[T + 1]
-    size_t b = (size_t)T * 16 + (size_t)(T + 1) * 8;
+    // records float4[T], vertices int2[T + 3] (a tile's T + 1 vertices, shifted by one when the
+    // tile starts at an odd vertex so that the bulk copy lands on a 16-byte boundary)
+    size_t b = (size_t)T * 16 + (size_t)(T + 3) * 8;
     return (b + 15) & ~(size_t)15;
 }
 
@@ -731,7 +734,9 @@ __global__ void __launch_bounds__(LG_THREADS, PPT == 4 ? 3 : 4) k_pip_large(Clas
 {
     extern __shared__ __align__(16) unsigned char dsm[];
     float4 *s_rec = reinterpret_cast<float4 *>(dsm);
-    int2 *s_v = reinterpret_cast<int2 *>(s_rec + T);
+    int2 *const s_vraw = reinterpret_cast<int2 *>(s_rec + T);   // 16-byte aligned
+    __shared__ __align__(8) unsigned long long s_bar;           // completion of the tile's bulk copy
+    __shared__ int s_fail;
     __shared__ int s_item[4];          // polygon, candidate block, edge slice, valid
     __shared__ int s_pb[4], s_tb[4];
     __shared__ int s_tf[4];            // tile frame: ox, oy, bound (float bits), wide
@@ -745,6 +750,11 @@ __global__ void __launch_bounds__(LG_THREADS, PPT == 4 ? 3 : 4) k_pip_large(Clas
     const int count = *((volatile int *)&ll->count);
     const bool scan = *((volatile int *)&ll->overflow) != 0;
     if (count == 0 && !scan) return;   // nothing listed: the header is already clear for the next call
+    if (tid == 0) {
+        mbar_init(&s_bar, 1);
+        s_fail = 0;
+    }
+    unsigned bar_phase = 0;
     long long scan_k = blockIdx.x;   // overflow mode: polygons blockIdx.x, + gridDim.x, ...
     const SlabHeader *sh = reinterpret_cast<const SlabHeader *>(a.slab);
     const bool slab_ok = sh && sh->valid && sh->n_polys == P;
@@ -848,10 +858,28 @@ __global__ void __launch_bounds__(LG_THREADS, PPT == 4 ? 3 : 4) k_pip_large(Clas
         for (int e0 = ea; !use_slabs && s_pb[0] <= s_pb[2] && e0 < eb; e0 += T) {
             const int nt = min(T, eb - e0);
             if (tid == 0) { s_tb[0] = s_pb[0]; s_tb[1] = s_pb[1]; s_tb[2] = s_pb[2]; s_tb[3] = s_pb[3]; }
+            // the tile's vertices e0 .. e0 + nt (the last one is vertex 0 when the tile closes the
+            // polygon): the 16-byte-aligned interior of the contiguous run by one bulk copy, the
+            // at most one vertex before and after it and the closing vertex by plain loads
+            const int ncont = e0 + nt < m ? nt + 1 : nt;
+            const unsigned long long src_lo = (unsigned long long)(a.verts + base + e0);
+            const unsigned long long src_hi = src_lo + 8ull * (unsigned long long)ncont;
+            const unsigned long long A = (src_lo + 15) & ~15ull, Bnd = src_hi & ~15ull;
+            int2 *s_v = s_vraw + ((src_lo & 15) ? 1 : 0);     // s_v[i] = vertex e0 + i
+            const bool bulk = Bnd > A;
+            if (bulk && tid == 0)
+                bulk_copy_g2s(s_v + (A - src_lo) / 8, reinterpret_cast<const void *>(A), (unsigned)(Bnd - A), &s_bar);
+            const int ia = bulk ? (int)((A - src_lo) / 8) : ncont;        // first vertex of the copy
+            const int ib = bulk ? (int)((Bnd - src_lo) / 8) : ncont;      // first vertex after it
             for (int i = tid; i <= nt; i += LG_THREADS) {
+                if (bulk && i >= ia && i < ib) continue;
                 int g = e0 + i;
                 if (g >= m) g -= m;
                 s_v[i] = __ldg(a.verts + base + g);
+            }
+            if (bulk) {
+                if (!mbar_wait(&s_bar, bar_phase, 1 << 22) && !mbar_wait(&s_bar, bar_phase, 1 << 22)) s_fail = 1;
+                bar_phase ^= 1u;
             }
             __syncthreads();
             int x0 = INT_MAX, y0 = INT_MAX, x1 = INT_MIN, y1 = INT_MIN;
@@ -941,6 +969,7 @@ __global__ void __launch_bounds__(LG_THREADS, PPT == 4 ? 3 : 4) k_pip_large(Clas
             if (st_fbp) atomicAdd(a.stats + ST_FALLBACK_POINTS, st_fbp);
             if (VERIFY && st_err) atomicAdd(a.stats + ST_FILTER_ERRORS, st_err);
             if (VERIFY && st_ver) atomicAdd(a.stats + ST_VERIFIED, st_ver);
+            if (tid == 0 && s_fail) atomicAdd(a.stats + ST_WAIT_TIMEOUTS, 1ULL);
         }
     }
     // the last CTA to finish empties the list for the next call

@@ -358,7 +358,7 @@ def test_large_polygons_full_range_and_near_the_frame_limit(api):
     finally:
         api.pip_set_verify(False)
     assert_same(got, oracle.classify(w.points, w.poly_offsets, w.verts), w.n_bits, "verification mode")
-    assert s["verified_pairs"] > 0 and s["filter_errors"] == 0
+    assert s["verified_pairs"] > 0 and s["filter_errors"] == 0 and s["wait_timeouts"] == 0
 
 
 # ------------------------------------------------------------------------------------------
@@ -392,6 +392,7 @@ def test_verification_mode_finds_no_unsound_decision(api, name, make_w):
     assert_same(got, want, w.n_bits, f"{name} (verification mode)")
     assert s["verified_pairs"] > 0
     assert s["filter_errors"] == 0, f"{s['filter_errors']} of {s['verified_pairs']} trusted decisions were wrong"
+    assert s["wait_timeouts"] == 0
 
 
 # ------------------------------------------------------------------------------------------
