@@ -411,19 +411,25 @@ __global__ void k_poly_candidates(const int4 *__restrict__ bb, const int32_t *__
             const long long cy0 = cell_coord(b.y, gy0, cell, ny), cy1 = cell_coord(b.w, gy0, cell, ny);
             for (long long cy = cy0; cy <= cy1; ++cy) {
                 const long long r0 = cell_start[cy * nx + cx0], r1 = cell_start[cy * nx + cx1 + 1];
-                for (long long i0 = r0; i0 < r1; i0 += 32) {
-                    const long long i = i0 + lane;
-                    bool in = false;
-                    if (i < r1) {
-                        const int2 p = spts[i];
-                        in = p.x >= b.x && p.x <= b.z && p.y >= b.y && p.y <= b.w;
+                // 128 points per step, four loads per lane in flight, tested in order
+                for (long long i0 = r0; i0 < r1; i0 += 128) {
+                    int2 pp[4];
+                    #pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const long long i = i0 + 32 * u + lane;
+                        pp[u] = i < r1 ? spts[i] : make_int2(0, 0);
                     }
-                    const unsigned m = __ballot_sync(FULL, in);
-                    if (FILL && in) {
-                        const long long dst = pos + n + __popc(m & ((1u << lane) - 1u));
-                        if (dst < capacity) cand_ids[dst] = sids[i];
+                    #pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const long long i = i0 + 32 * u + lane;
+                        const bool in = i < r1 && pp[u].x >= b.x && pp[u].x <= b.z && pp[u].y >= b.y && pp[u].y <= b.w;
+                        const unsigned m = __ballot_sync(FULL, in);
+                        if (FILL && in) {
+                            const long long dst = pos + n + __popc(m & ((1u << lane) - 1u));
+                            if (dst < capacity) cand_ids[dst] = sids[i];
+                        }
+                        n += __popc(m);
                     }
-                    n += __popc(m);
                 }
             }
         }
