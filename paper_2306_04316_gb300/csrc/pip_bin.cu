@@ -252,9 +252,20 @@ __global__ void k_point_keys(const int2 *__restrict__ pts, long long N, const Bi
 {
     const long long cell = h->cell, gx0 = h->gx0, gy0 = h->gy0;
     const int nx = h->gnx, ny = h->gny;
+    // every point lies in [g0, g0 + 2^32): 32-bit offsets and, for cells below 2^32, a 32-bit
+    // division instead of a 64-bit one
+    const bool narrow = cell <= 0xffffffffLL;
+    const unsigned ucell = (unsigned)cell;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
         const int2 p = __ldg(pts + i);
-        const unsigned id = (unsigned)(cell_coord(p.y, gy0, cell, ny) * nx + cell_coord(p.x, gx0, cell, nx));
+        unsigned id;
+        if (narrow) {
+            const unsigned cx = min((unsigned)((long long)p.x - gx0) / ucell, (unsigned)(nx - 1));
+            const unsigned cy = min((unsigned)((long long)p.y - gy0) / ucell, (unsigned)(ny - 1));
+            id = cy * (unsigned)nx + cx;
+        } else {
+            id = (unsigned)(cell_coord(p.y, gy0, cell, ny) * nx + cell_coord(p.x, gx0, cell, nx));
+        }
         keys[i] = id;
         vals[i] = (int)i;
         atomicAdd(cell_count + id, 1u);
