@@ -305,7 +305,12 @@ def run_join(args, rank, world):
     host_pts = [W.join_points(clusters, seed + 1000 + b, n_pts) for b in range(nb)]
     d_pts = [torch.from_numpy(x).cuda() for x in host_pts]
     stream = torch.cuda.Stream()
-    ws = api.bin_workspace(n_pts, P)
+    # independent batches run on several streams (each with its own binning workspace) so that
+    # their latency-bound kernels overlap; the graph forks from and joins back to `stream`
+    ns = max(1, min(args.streams, nb))
+    streams = [torch.cuda.Stream() for _ in range(ns)]
+    wss = [api.bin_workspace(n_pts, P) for _ in range(ns)]
+    ws = wss[0]
     co = [torch.empty(P + 1, dtype=torch.int32, device="cuda") for _ in range(nb)]
     tot = [torch.empty(1, dtype=torch.int64, device="cuda") for _ in range(nb)]
     with torch.cuda.stream(stream):
@@ -320,11 +325,16 @@ def run_join(args, rank, world):
     ovf = torch.zeros(nb, dtype=torch.int32, device="cuda")
 
     def one_pass(classify=True):
+        for s_ in streams:
+            s_.wait_stream(stream)
         for b in range(nb):
-            api.pip_bin_count(d_pts[b], d_po, d_v, workspace=ws, cand_offsets=co[b], d_total=tot[b], stream=stream)
-            api.pip_bin_fill(d_pts[b], d_po, d_v, ws, co[b], ids[b], d_overflow=ovf[b:b + 1], stream=stream)
+            s_, w_ = streams[b % ns], wss[b % ns]
+            api.pip_bin_count(d_pts[b], d_po, d_v, workspace=w_, cand_offsets=co[b], d_total=tot[b], stream=s_)
+            api.pip_bin_fill(d_pts[b], d_po, d_v, w_, co[b], ids[b], d_overflow=ovf[b:b + 1], stream=s_)
             if classify:
-                api.pip_classify(d_pts[b], d_po, d_v, co[b], ids[b], out=outs[b], stream=stream)
+                api.pip_classify(d_pts[b], d_po, d_v, co[b], ids[b], out=outs[b], stream=s_)
+        for s_ in streams:
+            stream.wait_stream(s_)
 
     with torch.cuda.stream(stream):
         one_pass()
@@ -393,7 +403,8 @@ def run_join(args, rank, world):
                 "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f32+i64", "data": "synthetic",
                 "config": {"workload": f"join: {P} polygons x {nb} batches of {n_pts} clustered points, "
-                                       f"{C} candidates from GPU binning, one CUDA-graph replay per step",
+                                       f"{C} candidates from GPU binning, one CUDA-graph replay per step "
+                                       f"({ns} streams)",
                            "pair_tests_per_step": T, "candidates_per_step": C, "binning_ms_per_step": bin_ms,
                            "classify_ms_per_step": ms - bin_ms, "tuning": list(api.pip_get_tuning()),
                            "autotuned": autotuned, "l2": "inputs larger than L2 (no flush)"},
@@ -434,6 +445,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--batches", type=int, default=20, help="join workload: point batches per step")
+    ap.add_argument("--streams", type=int, default=4,
+                    help="join workload: streams the batches are spread over inside the graph")
     ap.add_argument("--tuning", default="", help="edge_tile,pts_per_thread,ctas_per_sm (0 = keep)")
     ap.add_argument("--autotune", action="store_true",
                     help="pick the large-polygon kernel's tuning with the autotuner before timing "
