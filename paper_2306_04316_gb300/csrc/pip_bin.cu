@@ -3,19 +3,26 @@
 // Not part of the paper's method (the paper tests every point against one polygon); this is
 // the pre-pass that feeds the batched classify kernel.  Candidates of polygon k are all points
 // inside k's CLOSED bounding box -- a necessary condition for being inside k, so no inside
-// point is ever dropped.  Steps, all on the device, no host synchronisation:
-//   1. polygon bounding boxes (one warp per polygon), the points' bounding box, and the mean
-//      polygon extent;
-//   2. grid parameters (one thread): cell = requested size, or the mean polygon extent,
-//      doubled until the grid has at most 2^24 cells;
-//   3. cell id of every point, cell histogram, exclusive scan -> cell start offsets;
-//   4. stable LSD radix sort of (cell id, point id) in three passes of 8 bits (so
-//      ids ascend within a cell; each pass orders a tile in shared memory first so that its
-//      writes are coalesced), then a gather of the points into cell order;
-//   5. per polygon (one warp): walk the rows of cells its box covers -- each row is one
-//      contiguous range of the sorted points -- and count (pip_bin_count) or write
-//      (pip_bin_fill) the points inside the closed box, in that order.
-// The count pass writes per-polygon counts into cand_offsets and scans them in place.
+// point is ever dropped.  The polygons are binned, not the points, so no pass ever sorts the
+// points.  Steps, all on the device, no host synchronisation:
+//   1. polygon bounding boxes (one warp per polygon); lane l of the warp also counts the cells
+//      of edge 2^l that the box covers, for every level l at once;
+//   2. the level (one thread): the finest cell edge 2^l at which the (polygon, cell) pairs of
+//      the boxes covering at most 64 cells fit the pair list (4 per polygon + 1024), with at
+//      most 256 larger boxes -- those go on a short list that every point tests directly;
+//   3. the occupied cells in an open-addressing hash table keyed by the cell (cx, cy),
+//      cx = (x + 2^31) >> l: insert, count polygons per cell, scan, fill the per-cell lists
+//      (each entry a copy of the polygon's box, so that a point reads its cell's slot -- key,
+//      first entry and count in 16 bytes -- and then one contiguous run of boxes);
+//   4. per point (one thread): its cell's polygons and the short list, each box tested; the
+//      count pass (pip_bin_count) counts per polygon with atomics, scans the counts into
+//      cand_offsets and records the (polygon, point) pairs in the workspace; the fill pass
+//      (pip_bin_fill) places each recorded id by an atomic cursor (probing the points again
+//      only if more pairs were found than the workspace records: N / 4 + 4 per polygon);
+//   5. every polygon's id list sorted ascending (bitonic: one warp per polygon in its registers
+//      up to 32 ids or its shared memory up to 1024; longer lists queued for one CTA each, in
+//      shared memory up to 8192, else in place in global memory), so that the CSR is the same
+//      on every run.
 #include <algorithm>
 
 #include "pip_device.cuh"
@@ -23,31 +30,41 @@
 
 namespace pipdev {
 
-constexpr int BIN_MAX_CELLS_LOG2 = 24;
-constexpr long long BIN_MAX_CELLS = 1LL << BIN_MAX_CELLS_LOG2;
-constexpr int RADIX_THREADS = 256;
-constexpr int RADIX_ITEMS = 16;
-constexpr int RADIX_TILE = RADIX_THREADS * RADIX_ITEMS;
-constexpr int SCAN_TILE = 1024;     // elements per scan block (256 threads x 4)
+constexpr int BIN_CELL_CAP = 64;       // boxes covering more cells than this go on the short list
+constexpr int BIN_BIG_CAP = 256;       // most polygons on the short list
+constexpr unsigned long long BIN_EMPTY = ~0ull;   // an empty hash slot (cx < 2^31 for level >= 1)
+constexpr int SCAN_TILE = 1024;        // elements per scan block (256 threads x 4)
+constexpr int SORT_WARP_SMEM = 1024;   // ids a warp sorts in its own shared memory
+constexpr int SORT_CTA_SMEM = 8192;    // ids a CTA sorts in shared memory
 
 struct BinHeader {
-    int px0, py0, px1, py1;          // points' bounding box
-    long long cell;                  // cell edge in units
-    long long gx0, gy0;              // grid origin
-    int gnx, gny;                    // grid size in cells
-    unsigned long long ext_sum;      // sum over polygons of max(width, height)
-    unsigned long long n_nonempty;   // polygons with >= 1 vertex
+    unsigned long long cells[32];    // cells[l]: (polygon, cell) pairs of the boxes with <= BIN_CELL_CAP cells
+    unsigned long long big[32];      // big[l]: boxes with more cells than that, at cell edge 2^l
+    int level;                       // chosen cell edge 2^level
+    int n_big;                       // polygons on the short list
+    int requested_level;             // 0: automatic
+    int n_long;                      // id lists queued for the CTA-wide sort
     long long total;                 // candidates (int64)
-    int requested_cell;
-    int pad;
+    unsigned long long n_pairs;      // (polygon, point) pairs the count pass recorded
 };
 
-// Workspace layout (offsets in bytes, each 256-aligned).
+// Workspace layout (offsets in bytes, each 256-aligned).  Only the polygon count sizes it.
 struct BinLayout {
-    size_t header, poly_bb, keys_a, keys_b, vals_a, vals_b, spts, cell_start, hist, scan_tmp, total;
+    size_t header, poly_bb, ent, cnt, off, list_bb, list_id, big, cursor, long_list, pairs, scan_tmp, total;
+    long long H, lcap;               // hash slots (a power of two), pair-list capacity
+    long long pcap;                  // (polygon, point) pairs the count pass can record
+    int hbits;
+};
+
+// A slot of the cell table: the cell's key, then (first list entry, polygons) once built.
+struct __align__(16) CellEntry {
+    unsigned long long key;
+    int start, count;
 };
 
 static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+static long long pair_capacity(int P) { return 4LL * P + 1024; }
 
 long long scan_tmp_elems(long long n)
 {
@@ -62,18 +79,24 @@ long long scan_tmp_elems(long long n)
 static BinLayout bin_layout(long long N, int P)
 {
     BinLayout L;
-    const long long nblk = std::max<long long>(1, (N + RADIX_TILE - 1) / RADIX_TILE);
-    const long long scan_max = std::max<long long>({BIN_MAX_CELLS + 1, 256 * nblk, (long long)P + 1});
+    L.pcap = N / 4 + 4LL * P + 1024;
+    L.lcap = pair_capacity(P);
+    L.hbits = 1;
+    while ((1LL << L.hbits) < 4 * L.lcap) ++L.hbits;   // at most a quarter full
+    L.H = 1LL << L.hbits;
+    const long long scan_max = std::max<long long>(L.H, (long long)P + 1);
     size_t o = 0;
     L.header = o; o += align256(sizeof(BinHeader));
     L.poly_bb = o; o += align256((size_t)std::max(P, 1) * 16);
-    L.keys_a = o; o += align256((size_t)std::max<long long>(N, 1) * 4);
-    L.keys_b = o; o += align256((size_t)std::max<long long>(N, 1) * 4);
-    L.vals_a = o; o += align256((size_t)std::max<long long>(N, 1) * 4);
-    L.vals_b = o; o += align256((size_t)std::max<long long>(N, 1) * 4);
-    L.spts = o; o += align256((size_t)std::max<long long>(N, 1) * 8);
-    L.cell_start = o; o += align256((size_t)(BIN_MAX_CELLS + 1) * 4);
-    L.hist = o; o += align256((size_t)256 * nblk * 4);
+    L.ent = o; o += align256((size_t)L.H * sizeof(CellEntry));
+    L.cnt = o; o += align256((size_t)L.H * 4);
+    L.off = o; o += align256((size_t)L.H * 4);
+    L.list_bb = o; o += align256((size_t)L.lcap * 16);
+    L.list_id = o; o += align256((size_t)L.lcap * 4);
+    L.big = o; o += align256((size_t)BIN_BIG_CAP * 4);
+    L.cursor = o; o += align256((size_t)std::max(P, 1) * 4);
+    L.long_list = o; o += align256((size_t)std::max(P, 1) * 4);
+    L.pairs = o; o += align256((size_t)L.pcap * 8);
     L.scan_tmp = o; o += align256((size_t)scan_tmp_elems(scan_max) * 4);
     L.total = o;
     return L;
@@ -148,16 +171,36 @@ int scan_exclusive(unsigned *d, long long n, unsigned *tmp, cudaStream_t s)
 }
 
 // ------------------------------------------------------------------------------------------
-// bounding boxes and grid
+// polygon boxes and the level
 // ------------------------------------------------------------------------------------------
-__global__ void k_bin_init(BinHeader *h, int requested_cell, long long *d_total)
+__global__ void k_bin_init(BinHeader *h, int requested_level, long long *d_total)
 {
-    if (threadIdx.x == 0 && blockIdx.x == 0) {
-        h->px0 = INT_MAX; h->py0 = INT_MAX; h->px1 = INT_MIN; h->py1 = INT_MIN;
-        h->ext_sum = 0; h->n_nonempty = 0; h->total = 0;
-        h->requested_cell = requested_cell;
-        if (d_total) *d_total = 0;
+    const int t = threadIdx.x;
+    if (blockIdx.x == 0 && t < 32) {
+        h->cells[t] = 0;
+        h->big[t] = 0;
+        if (t == 0) {
+            h->level = 31;
+            h->n_big = 0;
+            h->requested_level = requested_level;
+            h->total = 0;
+            h->n_pairs = 0;
+            if (d_total) *d_total = 0;
+        }
     }
+}
+
+// cell coordinate of x at level l: (x + 2^31) >> l
+__device__ __forceinline__ unsigned cell_of(int x, int l) { return ((unsigned)x ^ 0x80000000u) >> l; }
+
+__device__ __forceinline__ unsigned long long cell_key(unsigned cx, unsigned cy)
+{
+    return ((unsigned long long)cy << 32) | cx;
+}
+
+__device__ __forceinline__ unsigned long long hash_slot(unsigned long long key, int hbits)
+{
+    return (key * 0x9E3779B97F4A7C15ull) >> (64 - hbits);
 }
 
 __global__ void k_poly_bbox(const int32_t *__restrict__ po, const int2 *__restrict__ verts, int P, int4 *bb,
@@ -166,7 +209,13 @@ __global__ void k_poly_bbox(const int32_t *__restrict__ po, const int2 *__restri
     const int lane = threadIdx.x & 31;
     const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
-    unsigned long long ext = 0, nne = 0;
+    __shared__ unsigned long long s_cells[32], s_big[32];
+    if (threadIdx.x < 32) {
+        s_cells[threadIdx.x] = 0;
+        s_big[threadIdx.x] = 0;
+    }
+    __syncthreads();
+    unsigned long long my_cells = 0, my_big = 0;   // lane l: level l
     for (long long k = warp; k < P; k += nw) {
         const int v0 = __ldg(po + k), v1 = __ldg(po + k + 1);
         int x0 = INT_MAX, y0 = INT_MAX, x1 = INT_MIN, y1 = INT_MIN;
@@ -181,279 +230,348 @@ __global__ void k_poly_bbox(const int32_t *__restrict__ po, const int2 *__restri
             x1 = max(x1, __shfl_xor_sync(FULL, x1, o));
             y1 = max(y1, __shfl_xor_sync(FULL, y1, o));
         }
-        if (lane == 0) {
-            bb[k] = make_int4(x0, y0, x1, y1);
-            if (v1 > v0) {
-                ext += (unsigned long long)max((long long)x1 - x0, (long long)y1 - y0);
-                ++nne;
-            }
+        if (lane == 0) bb[k] = make_int4(x0, y0, x1, y1);
+        if (v1 > v0 && lane >= 1) {
+            const unsigned long long n = (unsigned long long)(cell_of(x1, lane) - cell_of(x0, lane) + 1) *
+                                         (cell_of(y1, lane) - cell_of(y0, lane) + 1);
+            if (n <= BIN_CELL_CAP) my_cells += n; else ++my_big;
         }
     }
-    if (lane == 0 && nne) {
-        atomicAdd(&h->ext_sum, ext);
-        atomicAdd(&h->n_nonempty, nne);
+    if (lane >= 1) {
+        if (my_cells) atomicAdd(&s_cells[lane], my_cells);
+        if (my_big) atomicAdd(&s_big[lane], my_big);
+    }
+    __syncthreads();
+    if (threadIdx.x >= 1 && threadIdx.x < 32) {
+        if (s_cells[threadIdx.x]) atomicAdd(&h->cells[threadIdx.x], s_cells[threadIdx.x]);
+        if (s_big[threadIdx.x]) atomicAdd(&h->big[threadIdx.x], s_big[threadIdx.x]);
     }
 }
 
-__global__ void k_points_bbox(const int2 *__restrict__ pts, long long N, BinHeader *h)
+// The finest level at or above the requested one whose pairs fit the list and whose larger boxes
+// fit the short list.  Level 31 always qualifies: every box covers at most 2 x 2 cells.
+__global__ void k_bin_level(BinHeader *h, long long lcap)
 {
-    int x0 = INT_MAX, y0 = INT_MAX, x1 = INT_MIN, y1 = INT_MIN;
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
-        const int2 p = __ldg(pts + i);
-        x0 = min(x0, p.x); y0 = min(y0, p.y); x1 = max(x1, p.x); y1 = max(y1, p.y);
-    }
-    #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        x0 = min(x0, __shfl_xor_sync(FULL, x0, o));
-        y0 = min(y0, __shfl_xor_sync(FULL, y0, o));
-        x1 = max(x1, __shfl_xor_sync(FULL, x1, o));
-        y1 = max(y1, __shfl_xor_sync(FULL, y1, o));
-    }
-    if ((threadIdx.x & 31) == 0) {
-        atomicMin(&h->px0, x0); atomicMin(&h->py0, y0); atomicMax(&h->px1, x1); atomicMax(&h->py1, y1);
-    }
-}
-
-__global__ void k_grid_params(BinHeader *h)
-{
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    long long w = 1, hgt = 1;
-    if (h->px0 <= h->px1) {
-        w = (long long)h->px1 - h->px0 + 1;
-        hgt = (long long)h->py1 - h->py0 + 1;
-        h->gx0 = h->px0;
-        h->gy0 = h->py0;
-    } else {
-        h->gx0 = 0;
-        h->gy0 = 0;
-    }
-    long long cell = h->requested_cell;
-    if (cell <= 0) cell = h->n_nonempty ? (long long)(h->ext_sum / h->n_nonempty) : 1;
-    if (cell < 1) cell = 1;
-    long long nx = (w + cell - 1) / cell, ny = (hgt + cell - 1) / cell;
-    while (nx * ny > BIN_MAX_CELLS) {
-        cell *= 2;
-        nx = (w + cell - 1) / cell;
-        ny = (hgt + cell - 1) / cell;
-    }
-    h->cell = cell;
-    h->gnx = (int)nx;
-    h->gny = (int)ny;
-}
-
-__device__ __forceinline__ long long cell_coord(long long v, long long g0, long long cell, int n)
-{
-    long long c = v < g0 ? 0 : (v - g0) / cell;
-    return c >= n ? n - 1 : c;
-}
-
-__global__ void k_point_keys(const int2 *__restrict__ pts, long long N, const BinHeader *__restrict__ h,
-                             unsigned *keys, int *vals, unsigned *cell_count)
-{
-    const long long cell = h->cell, gx0 = h->gx0, gy0 = h->gy0;
-    const int nx = h->gnx, ny = h->gny;
-    // every point lies in [g0, g0 + 2^32): 32-bit offsets and, for cells below 2^32, a 32-bit
-    // division instead of a 64-bit one
-    const bool narrow = cell <= 0xffffffffLL;
-    const unsigned ucell = (unsigned)cell;
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
-        const int2 p = __ldg(pts + i);
-        unsigned id;
-        if (narrow) {
-            const unsigned cx = min((unsigned)((long long)p.x - gx0) / ucell, (unsigned)(nx - 1));
-            const unsigned cy = min((unsigned)((long long)p.y - gy0) / ucell, (unsigned)(ny - 1));
-            id = cy * (unsigned)nx + cx;
-        } else {
-            id = (unsigned)(cell_coord(p.y, gy0, cell, ny) * nx + cell_coord(p.x, gx0, cell, nx));
-        }
-        keys[i] = id;
-        vals[i] = (int)i;
-        atomicAdd(cell_count + id, 1u);
-    }
+    if (blockIdx.x != 0 || threadIdx.x >= 32) return;
+    const int l = threadIdx.x;
+    const bool ok = l == 31 || (l >= max(1, h->requested_level) && h->cells[l] <= (unsigned long long)lcap &&
+                                h->big[l] <= (unsigned long long)BIN_BIG_CAP);
+    const unsigned m = __ballot_sync(FULL, ok);
+    if (l == 0) h->level = __ffs(m) - 1;
 }
 
 // ------------------------------------------------------------------------------------------
-// stable LSD radix sort pass (digit of `bits` bits at `shift`)
+// the cell table
 // ------------------------------------------------------------------------------------------
-__global__ void __launch_bounds__(RADIX_THREADS) k_radix_hist(const unsigned *__restrict__ keys, long long N,
-                                                             int shift, int nblk, unsigned *hist)
+// INSERT: claim every covered cell's slot and count the polygon there; else find the slot and
+// append the polygon to the cell's list.  Boxes with too many cells go on the short list.
+template <bool INSERT>
+__global__ void k_cells(const int4 *__restrict__ bb, const int32_t *__restrict__ po, int P, BinHeader *h,
+                        CellEntry *ent, unsigned *cnt, unsigned *off, int4 *list_bb, int *list_id, int *big,
+                        int hbits)
 {
-    __shared__ unsigned cnt[256];
-    cnt[threadIdx.x] = 0;
-    __syncthreads();
-    const long long base = (long long)blockIdx.x * RADIX_TILE;
-    #pragma unroll 4
-    for (int r = 0; r < RADIX_ITEMS; ++r) {
-        const long long i = base + r * RADIX_THREADS + threadIdx.x;
-        if (i < N) atomicAdd(&cnt[(keys[i] >> shift) & 255u], 1u);
-    }
-    __syncthreads();
-    hist[(long long)threadIdx.x * nblk + blockIdx.x] = cnt[threadIdx.x];
-}
-
-__global__ void __launch_bounds__(RADIX_THREADS) k_radix_scatter(const unsigned *__restrict__ kin,
-                                                                const int *__restrict__ vin, unsigned *kout,
-                                                                int *vout, long long N, int shift, int nblk,
-                                                                const unsigned *__restrict__ hist)
-{
-    // The tile's keys are ranked stably within their digit (tile order = input order), placed
-    // in digit order in shared memory, then written out so that consecutive threads write
-    // consecutive positions of one digit's run (coalesced), at the run's global start.
-    __shared__ unsigned s_base[256];    // global start of digit d's keys from this tile
-    __shared__ unsigned s_run[256];     // keys of digit d ranked so far (then: tile count)
-    __shared__ unsigned s_lstart[256];  // tile-local start of digit d
-    __shared__ unsigned s_wc[RADIX_THREADS / 32][256];
-    __shared__ unsigned s_key[RADIX_TILE];
-    __shared__ int s_val[RADIX_TILE];
-    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-    s_base[tid] = hist[(long long)tid * nblk + blockIdx.x];
-    s_run[tid] = 0;
-    #pragma unroll
-    for (int q = 0; q < RADIX_THREADS / 32; ++q) s_wc[q][tid] = 0;
-    const long long base = (long long)blockIdx.x * RADIX_TILE;
-    const int nt = (int)min((long long)RADIX_TILE, N - base);
-    unsigned key[RADIX_ITEMS];
-    int val[RADIX_ITEMS];
-    unsigned packed[RADIX_ITEMS];   // digit << 16 | rank within the digit
-    #pragma unroll
-    for (int r = 0; r < RADIX_ITEMS; ++r) {
-        const int i = r * RADIX_THREADS + tid;
-        key[r] = i < nt ? kin[base + i] : 0u;
-        val[r] = i < nt ? vin[base + i] : 0;
-    }
-    __syncthreads();
-    const unsigned lt = (1u << lane) - 1u;
-    #pragma unroll
-    for (int r = 0; r < RADIX_ITEMS; ++r) {
-        const bool valid = r * RADIX_THREADS + tid < nt;
-        const unsigned d = valid ? ((key[r] >> shift) & 255u) : 256u;
-        const unsigned peers = __match_any_sync(FULL, d);
-        const unsigned rank = __popc(peers & lt);
-        if (valid && (peers & lt) == 0) s_wc[w][d] = __popc(peers);
-        __syncthreads();
-        unsigned off = 0;
-        if (valid) {
-            off = s_run[d] + rank;
-            for (int q = 0; q < w; ++q) off += s_wc[q][d];
-        }
-        packed[r] = (d << 16) | off;
-        __syncthreads();
-        unsigned add = 0;
-        #pragma unroll
-        for (int q = 0; q < RADIX_THREADS / 32; ++q) { add += s_wc[q][tid]; s_wc[q][tid] = 0; }
-        s_run[tid] += add;
-        __syncthreads();
-    }
-    // tile-local digit starts: exclusive scan of s_run over the 256 digits
-    {
-        const unsigned c = s_run[tid];
-        unsigned incl = c;
-        #pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const unsigned t = __shfl_up_sync(FULL, incl, o);
-            if (lane >= o) incl += t;
-        }
-        if (lane == 31) s_wc[0][w] = incl;
-        __syncthreads();
-        if (w == 0) {
-            const unsigned x = lane < RADIX_THREADS / 32 ? s_wc[0][lane] : 0u;
-            unsigned xi = x;
-            #pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const unsigned t = __shfl_up_sync(FULL, xi, o);
-                if (lane >= o) xi += t;
-            }
-            if (lane < RADIX_THREADS / 32) s_wc[1][lane] = xi - x;
-        }
-        __syncthreads();
-        s_lstart[tid] = s_wc[1][w] + incl - c;
-        __syncthreads();
-    }
-    #pragma unroll
-    for (int r = 0; r < RADIX_ITEMS; ++r) {
-        if (r * RADIX_THREADS + tid < nt) {
-            const unsigned d = packed[r] >> 16;
-            const unsigned pos = s_lstart[d] + (packed[r] & 0xffffu);
-            s_key[pos] = key[r];
-            s_val[pos] = val[r];
-        }
-    }
-    __syncthreads();
-    for (int i = tid; i < nt; i += RADIX_THREADS) {
-        const unsigned k = s_key[i];
-        const unsigned d = (k >> shift) & 255u;
-        const unsigned g = s_base[d] + (unsigned)i - s_lstart[d];
-        kout[g] = k;
-        vout[g] = s_val[i];
-    }
-}
-
-__global__ void k_gather_sorted(const int2 *__restrict__ pts, const int *__restrict__ ids, long long N, int2 *spts)
-{
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x)
-        spts[i] = __ldg(pts + __ldg(ids + i));
-}
-
-// ------------------------------------------------------------------------------------------
-// per-polygon candidate count / fill (one warp per polygon)
-// ------------------------------------------------------------------------------------------
-template <bool FILL>
-__global__ void k_poly_candidates(const int4 *__restrict__ bb, const int32_t *__restrict__ po, int P,
-                                  const BinHeader *__restrict__ h, const unsigned *__restrict__ cell_start,
-                                  const int2 *__restrict__ spts, const int *__restrict__ sids,
-                                  unsigned *counts, const int32_t *__restrict__ cand_offsets,
-                                  int32_t *cand_ids, long long capacity, long long *d_total)
-{
-    const int lane = threadIdx.x & 31;
-    const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const long long nwarp = ((long long)gridDim.x * blockDim.x) >> 5;
-    const long long cell = h->cell, gx0 = h->gx0, gy0 = h->gy0;
-    const int nx = h->gnx, ny = h->gny;
-    const bool have_pts = h->px0 <= h->px1;
-    unsigned long long tot = 0;
-    if (!FILL && warp == 0 && lane == 0) counts[P] = 0;
-    for (long long k = warp; k < P; k += nwarp) {
+    const int l = h->level;
+    const unsigned long long hmask = (1ull << hbits) - 1;
+    for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < P; k += (long long)gridDim.x * blockDim.x) {
+        if (__ldg(po + k + 1) <= __ldg(po + k)) continue;   // no vertices, no box
         const int4 b = bb[k];
-        long long n = 0;
-        long long pos = FILL ? (long long)cand_offsets[k] : 0;
-        const bool nonempty = __ldg(po + k + 1) > __ldg(po + k);
-        if (nonempty && have_pts && b.z >= h->px0 && b.x <= h->px1 && b.w >= h->py0 && b.y <= h->py1) {
-            const long long cx0 = cell_coord(b.x, gx0, cell, nx), cx1 = cell_coord(b.z, gx0, cell, nx);
-            const long long cy0 = cell_coord(b.y, gy0, cell, ny), cy1 = cell_coord(b.w, gy0, cell, ny);
-            for (long long cy = cy0; cy <= cy1; ++cy) {
-                const long long r0 = cell_start[cy * nx + cx0], r1 = cell_start[cy * nx + cx1 + 1];
-                // 128 points per step, four loads per lane in flight, tested in order
-                for (long long i0 = r0; i0 < r1; i0 += 128) {
-                    int2 pp[4];
-                    #pragma unroll
-                    for (int u = 0; u < 4; ++u) {
-                        const long long i = i0 + 32 * u + lane;
-                        pp[u] = i < r1 ? spts[i] : make_int2(0, 0);
-                    }
-                    #pragma unroll
-                    for (int u = 0; u < 4; ++u) {
-                        const long long i = i0 + 32 * u + lane;
-                        const bool in = i < r1 && pp[u].x >= b.x && pp[u].x <= b.z && pp[u].y >= b.y && pp[u].y <= b.w;
-                        const unsigned m = __ballot_sync(FULL, in);
-                        if (FILL && in) {
-                            const long long dst = pos + n + __popc(m & ((1u << lane) - 1u));
-                            if (dst < capacity) cand_ids[dst] = sids[i];
+        const unsigned cx0 = cell_of(b.x, l), cx1 = cell_of(b.z, l), cy0 = cell_of(b.y, l), cy1 = cell_of(b.w, l);
+        if ((unsigned long long)(cx1 - cx0 + 1) * (cy1 - cy0 + 1) > BIN_CELL_CAP) {
+            if (INSERT) {
+                const int i = atomicAdd(&h->n_big, 1);
+                if (i < BIN_BIG_CAP) big[i] = (int)k;
+            }
+            continue;
+        }
+        for (unsigned cy = cy0; cy <= cy1; ++cy)
+            for (unsigned cx = cx0; cx <= cx1; ++cx) {
+                const unsigned long long key = cell_key(cx, cy);
+                unsigned long long s = hash_slot(key, hbits);
+                // the table is at most half full, so a free or matching slot is always found
+                for (unsigned long long it = 0; it <= hmask; ++it, s = (s + 1) & hmask) {
+                    if (INSERT) {
+                        const unsigned long long prev = atomicCAS(&ent[s].key, BIN_EMPTY, key);
+                        if (prev == BIN_EMPTY || prev == key) {
+                            atomicAdd(cnt + s, 1u);
+                            break;
                         }
-                        n += __popc(m);
+                    } else if (ent[s].key == key) {
+                        const unsigned j = atomicAdd(off + s, 1u);
+                        list_bb[j] = b;
+                        list_id[j] = (int)k;
+                        break;
                     }
                 }
             }
-        }
-        if (!FILL && lane == 0) {
-            counts[k] = (unsigned)n;
-            tot += (unsigned long long)n;
-        }
     }
-    if (!FILL && lane == 0 && tot) atomicAdd(reinterpret_cast<unsigned long long *>(d_total), tot);
 }
 
-__global__ void k_bin_finish(BinHeader *h, const long long *d_total, const int32_t *cand_offsets, int P,
-                             long long capacity, int32_t *d_overflow)
+// (first list entry, count) of every occupied slot, after the fill advanced off[] to the list ends
+__global__ void k_cells_pack(const unsigned *cnt, const unsigned *off, CellEntry *ent, long long H)
+{
+    for (long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x; s < H; s += (long long)gridDim.x * blockDim.x) {
+        const unsigned c = cnt[s];
+        if (c) {
+            ent[s].start = (int)(off[s] - c);
+            ent[s].count = (int)c;
+        }
+    }
+}
+
+// ------------------------------------------------------------------------------------------
+// per point: the polygons of its cell and the short list
+// ------------------------------------------------------------------------------------------
+constexpr int PROBE_THREADS = 256;
+constexpr int PROBE_STAGE = 1024;      // pairs a CTA stages in shared memory per pass over 256 points
+
+// The polygons whose closed box holds point i: those of its cell and those of the short list.
+template <typename Emit>
+__device__ __forceinline__ void probe_point(int2 p, long long i, int l, unsigned long long hmask, int hbits,
+                                            const CellEntry *__restrict__ ent, const int4 *__restrict__ list_bb,
+                                            const int *__restrict__ list_id, const int *__restrict__ big, int nbig,
+                                            const int4 *__restrict__ bb, Emit emit)
+{
+    const unsigned long long key = cell_key(cell_of(p.x, l), cell_of(p.y, l));
+    unsigned long long s = hash_slot(key, hbits);
+    for (unsigned long long it = 0; it <= hmask; ++it, s = (s + 1) & hmask) {
+        const int4 e = __ldg(reinterpret_cast<const int4 *>(ent + s));   // key, start, count
+        const unsigned long long kk = ((unsigned long long)(unsigned)e.y << 32) | (unsigned)e.x;
+        if (kk == key) {
+            for (int j = e.z; j < e.z + e.w; ++j) {
+                const int4 b = __ldg(list_bb + j);
+                if (p.x >= b.x && p.x <= b.z && p.y >= b.y && p.y <= b.w) emit(__ldg(list_id + j), i);
+            }
+            break;
+        }
+        if (kk == BIN_EMPTY) break;
+    }
+    for (int j = 0; j < nbig; ++j) {
+        const int k = __ldg(big + j);
+        const int4 b = __ldg(bb + k);
+        if (p.x >= b.x && p.x <= b.z && p.y >= b.y && p.y <= b.w) emit(k, i);
+    }
+}
+
+// Count pass: per polygon counts (atomics), the total, and every (polygon, point) pair recorded
+// for the fill pass -- staged per warp in shared memory and appended with one atomic per flush,
+// in any order (the fill's sort fixes the order); pairs past the capacity are dropped and the
+// fill pass then probes the points again.  Warps run on their own: no CTA barrier.
+__global__ void __launch_bounds__(PROBE_THREADS) k_probe_count(
+    const int2 *__restrict__ pts, long long N, BinHeader *h, const CellEntry *__restrict__ ent,
+    const int4 *__restrict__ list_bb, const int *__restrict__ list_id, const int *__restrict__ big,
+    const int4 *__restrict__ bb, int hbits, unsigned *counts, int2 *pairs, long long pcap, long long *d_total)
+{
+    constexpr int WS = PROBE_STAGE / (PROBE_THREADS / 32);   // a warp's stage
+    __shared__ int2 s_pair[PROBE_STAGE];
+    __shared__ int s_n[PROBE_THREADS / 32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int2 *stage = s_pair + w * WS;
+    const int l = h->level;
+    const int nbig = min(h->n_big, BIN_BIG_CAP);
+    const unsigned long long hmask = (1ull << hbits) - 1;
+    unsigned long long tot = 0;
+    auto emit = [&](int k, long long i) {
+        atomicAdd(counts + k, 1u);
+        ++tot;
+        const int j = atomicAdd(&s_n[w], 1);
+        if (j < WS) {
+            stage[j] = make_int2(k, (int)i);
+        } else {   // the stage is full: straight to the global list
+            const unsigned long long g = atomicAdd(&h->n_pairs, 1ull);
+            if (g < (unsigned long long)pcap) pairs[g] = make_int2(k, (int)i);
+        }
+    };
+    auto flush = [&]() {
+        __syncwarp();
+        const int n = min(s_n[w], WS);
+        unsigned long long b = 0;
+        if (lane == 0 && n) b = atomicAdd(&h->n_pairs, (unsigned long long)n);
+        b = __shfl_sync(FULL, b, 0);
+        for (int j = lane; j < n; j += 32)
+            if (b + j < (unsigned long long)pcap) pairs[b + j] = stage[j];
+        __syncwarp();
+        if (lane == 0) s_n[w] = 0;
+        __syncwarp();
+    };
+    if (lane == 0) s_n[w] = 0;
+    __syncwarp();
+    const long long gw = ((long long)blockIdx.x * PROBE_THREADS + threadIdx.x) >> 5;
+    const long long nw = ((long long)gridDim.x * PROBE_THREADS) >> 5;
+    for (long long base = gw * 32; base < N; base += nw * 32) {
+        const long long i = base + lane;
+        if (i < N) probe_point(__ldg(pts + i), i, l, hmask, hbits, ent, list_bb, list_id, big, nbig, bb, emit);
+        __syncwarp();
+        if (s_n[w] >= WS / 2) flush();
+    }
+    flush();
+    #pragma unroll
+    for (int o = 16; o > 0; o >>= 1) tot += __shfl_down_sync(FULL, tot, o);
+    if (lane == 0 && tot) atomicAdd(reinterpret_cast<unsigned long long *>(d_total), tot);
+}
+
+// Fill pass: every id placed at its polygon's offset plus an atomic cursor -- from the pairs the
+// count pass recorded, or, when they did not all fit, by probing the points again.
+__global__ void __launch_bounds__(PROBE_THREADS) k_probe_fill(
+    const int2 *__restrict__ pts, long long N, const BinHeader *__restrict__ h, const CellEntry *__restrict__ ent,
+    const int4 *__restrict__ list_bb, const int *__restrict__ list_id, const int *__restrict__ big,
+    const int4 *__restrict__ bb, int hbits, const int2 *__restrict__ pairs, long long pcap,
+    const int32_t *__restrict__ cand_offsets, unsigned *cursor, int32_t *cand_ids, long long capacity)
+{
+    auto place = [&](int k, long long i) {
+        const long long pos = (long long)__ldg(cand_offsets + k) + atomicAdd(cursor + k, 1u);
+        if (pos < capacity) cand_ids[pos] = (int32_t)i;
+    };
+    const unsigned long long np = h->n_pairs;
+    const long long t0 = (long long)blockIdx.x * blockDim.x + threadIdx.x, nt = (long long)gridDim.x * blockDim.x;
+    if (np <= (unsigned long long)pcap) {
+        for (long long j = t0; j < (long long)np; j += nt) {
+            const int2 q = __ldg(pairs + j);
+            place(q.x, q.y);
+        }
+    } else {
+        const int l = h->level;
+        const int nbig = min(h->n_big, BIN_BIG_CAP);
+        const unsigned long long hmask = (1ull << hbits) - 1;
+        for (long long i = t0; i < N; i += nt)
+            probe_point(__ldg(pts + i), i, l, hmask, hbits, ent, list_bb, list_id, big, nbig, bb, place);
+    }
+}
+
+// ------------------------------------------------------------------------------------------
+// per polygon: its ids sorted ascending
+// ------------------------------------------------------------------------------------------
+// 32 values, one per lane, sorted ascending across the warp (bitonic network whose comparators
+// all put the smaller value at the lower lane).
+__device__ __forceinline__ int warp_sort32(int v, int lane)
+{
+    #pragma unroll
+    for (int kk = 2; kk <= 32; kk <<= 1) {
+        int o = __shfl_xor_sync(FULL, v, kk - 1);                  // mirror within blocks of kk
+        v = (lane & (kk - 1)) < (kk >> 1) ? min(v, o) : max(v, o);
+        #pragma unroll
+        for (int j = kk >> 2; j > 0; j >>= 1) {
+            o = __shfl_xor_sync(FULL, v, j);
+            v = (lane & j) ? max(v, o) : min(v, o);
+        }
+    }
+    return v;
+}
+
+// V[0..n) sorted ascending by threads t0, t0 + nt, ... of a group that `sync` synchronises: the
+// same network over the next power of two, positions n and beyond counting as +infinity (a
+// comparator never moves one of them below n, so they are never touched).
+template <typename Sync>
+__device__ void bitonic_sort(int *V, int n, int t0, int nt, Sync sync)
+{
+    int P2 = 1;
+    while (P2 < n) P2 <<= 1;
+    for (int kk = 2; kk <= P2; kk <<= 1) {
+        for (int j = kk >> 1; j > 0; j >>= 1) {
+            const int lj = __ffs(j) - 1;
+            for (int t = t0; t < (P2 >> 1); t += nt) {
+                const int blk = t >> lj, r = t & (j - 1);
+                const int i = (blk << (lj + 1)) + r;
+                const int q = j == (kk >> 1) ? (blk << (lj + 1)) + kk - 1 - r : i + j;
+                if (q < n) {
+                    const int x = V[i], y = V[q];
+                    if (x > y) {
+                        V[i] = y;
+                        V[q] = x;
+                    }
+                }
+            }
+            sync();
+        }
+    }
+}
+
+// One warp per 32 consecutive polygons: lists of up to 8 ids sorted by their own lane in
+// registers, lists of up to SORT_WARP_SMEM ids by the whole warp (in registers up to 32, else
+// in its shared memory); longer lists are queued for k_seg_sort_long.
+__global__ void __launch_bounds__(256) k_seg_sort(const int32_t *__restrict__ cand_offsets, int P, int32_t *ids,
+                                                  long long capacity, BinHeader *h, int *long_list)
+{
+    __shared__ int s_v[8 * SORT_WARP_SMEM];
+    const int lane = threadIdx.x & 31;
+    int *wv = s_v + (threadIdx.x >> 5) * SORT_WARP_SMEM;
+    const long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+    for (long long k0 = gw * 32; k0 < P; k0 += nw * 32) {
+        const long long kl = k0 + lane;
+        long long my_a = 0, my_n = 0;
+        if (kl < P) {
+            my_a = min((long long)cand_offsets[kl], capacity);
+            my_n = min((long long)cand_offsets[kl + 1], capacity) - my_a;
+        }
+        if (my_n > 1 && my_n <= 8) {
+            int v[8];
+            #pragma unroll
+            for (int i = 0; i < 8; ++i) v[i] = i < my_n ? ids[my_a + i] : INT_MAX;
+            #pragma unroll
+            for (int kk = 2; kk <= 8; kk <<= 1) {
+                #pragma unroll
+                for (int j = kk >> 1; j > 0; j >>= 1) {
+                    #pragma unroll
+                    for (int i = 0; i < 8; ++i) {
+                        const int q = j == (kk >> 1) ? (i ^ (kk - 1)) : (i ^ j);
+                        if (q > i) {
+                            const int x = min(v[i], v[q]), y = max(v[i], v[q]);
+                            v[i] = x;
+                            v[q] = y;
+                        }
+                    }
+                }
+            }
+            #pragma unroll
+            for (int i = 0; i < 8; ++i)
+                if (i < my_n) ids[my_a + i] = v[i];
+        }
+        for (unsigned m = __ballot_sync(FULL, my_n > 8); m; m &= m - 1) {
+            const int src = __ffs(m) - 1;
+            const long long a = __shfl_sync(FULL, my_a, src), n = __shfl_sync(FULL, my_n, src);
+            if (n <= 32) {
+                int v = lane < n ? ids[a + lane] : INT_MAX;
+                v = warp_sort32(v, lane);
+                if (lane < n) ids[a + lane] = v;
+            } else if (n <= SORT_WARP_SMEM) {
+                for (int i = lane; i < n; i += 32) wv[i] = ids[a + i];
+                __syncwarp();
+                bitonic_sort(wv, (int)n, lane, 32, [] { __syncwarp(); });
+                for (int i = lane; i < n; i += 32) ids[a + i] = wv[i];
+                __syncwarp();
+            } else if (lane == 0) {
+                long_list[atomicAdd(&h->n_long, 1)] = (int)(k0 + src);
+            }
+        }
+    }
+}
+
+// The queued longer lists, one CTA per polygon: in shared memory up to SORT_CTA_SMEM ids, else in
+// place in global memory.
+__global__ void __launch_bounds__(256) k_seg_sort_long(const int32_t *__restrict__ cand_offsets, int32_t *ids,
+                                                       long long capacity, const BinHeader *h,
+                                                       const int *long_list)
+{
+    __shared__ int s_v[SORT_CTA_SMEM];
+    const int tid = threadIdx.x;
+    const int nl = h->n_long;
+    for (int t = blockIdx.x; t < nl; t += gridDim.x) {
+        const int k = long_list[t];
+        const long long a = min((long long)cand_offsets[k], capacity);
+        const long long n = min((long long)cand_offsets[k + 1], capacity) - a;
+        if (n <= SORT_CTA_SMEM) {
+            for (int i = tid; i < n; i += 256) s_v[i] = ids[a + i];
+            __syncthreads();
+            bitonic_sort(s_v, (int)n, tid, 256, [] { __syncthreads(); });
+            for (int i = tid; i < n; i += 256) ids[a + i] = s_v[i];
+        } else {
+            bitonic_sort(ids + a, (int)n, tid, 256, [] { __syncthreads(); });
+        }
+        __syncthreads();
+    }
+}
+
+__global__ void k_bin_finish(BinHeader *h, const long long *d_total, long long capacity, int32_t *d_overflow)
 {
     if (threadIdx.x == 0 && blockIdx.x == 0) {
         if (d_total) h->total = *d_total;
@@ -473,50 +591,46 @@ int launch_bin_count(const int2 *points, long long N, const int32_t *po, const i
     char *w = static_cast<char *>(ws);
     BinHeader *h = reinterpret_cast<BinHeader *>(w + L.header);
     int4 *bb = reinterpret_cast<int4 *>(w + L.poly_bb);
-    unsigned *ka = reinterpret_cast<unsigned *>(w + L.keys_a), *kb = reinterpret_cast<unsigned *>(w + L.keys_b);
-    int *va = reinterpret_cast<int *>(w + L.vals_a), *vb = reinterpret_cast<int *>(w + L.vals_b);
-    int2 *spts = reinterpret_cast<int2 *>(w + L.spts);
-    unsigned *cstart = reinterpret_cast<unsigned *>(w + L.cell_start);
-    unsigned *hist = reinterpret_cast<unsigned *>(w + L.hist);
+    CellEntry *ent = reinterpret_cast<CellEntry *>(w + L.ent);
+    unsigned *cnt = reinterpret_cast<unsigned *>(w + L.cnt);
+    unsigned *off = reinterpret_cast<unsigned *>(w + L.off);
+    int4 *list_bb = reinterpret_cast<int4 *>(w + L.list_bb);
+    int *list_id = reinterpret_cast<int *>(w + L.list_id);
+    int *big = reinterpret_cast<int *>(w + L.big);
     unsigned *tmp = reinterpret_cast<unsigned *>(w + L.scan_tmp);
     const int grid = n_sm * 8;
+    int requested = 0;   // cell edge rounded up to a power of two
+    if (cell_size > 0) {
+        requested = 1;
+        while (requested < 31 && (1LL << requested) < cell_size) ++requested;
+    }
     int e;
 
-    k_bin_init<<<1, 32, 0, s>>>(h, cell_size, d_total);
-    if (P > 0) k_poly_bbox<<<grid, 256, 0, s>>>(po, verts, P, bb, h);
-    if (N > 0) k_points_bbox<<<grid, 256, 0, s>>>(points, N, h);
-    k_grid_params<<<1, 32, 0, s>>>(h);
-    note_launch(2 + (P > 0) + (N > 0));
-    if ((e = (int)cudaMemsetAsync(cstart, 0, (size_t)(BIN_MAX_CELLS + 1) * 4, s))) return e;
-    if (N > 0) {
-        k_point_keys<<<grid, 256, 0, s>>>(points, N, h, ka, va, cstart);
-        note_launch();
-        if ((e = scan_exclusive(cstart, BIN_MAX_CELLS + 1, tmp, s))) return e;
-        const int nblk = (int)((N + RADIX_TILE - 1) / RADIX_TILE);
-        const int shifts[3] = {0, 8, 16};
-        for (int pass = 0; pass < 3; ++pass) {
-            k_radix_hist<<<nblk, RADIX_THREADS, 0, s>>>(ka, N, shifts[pass], nblk, hist);
-            note_launch();
-            if ((e = scan_exclusive(hist, 256LL * nblk, tmp, s))) return e;
-            k_radix_scatter<<<nblk, RADIX_THREADS, 0, s>>>(ka, va, kb, vb, N, shifts[pass], nblk, hist);
-            note_launch();
-            std::swap(ka, kb);
-            std::swap(va, vb);
-        }
-        // after three passes the sorted ids are in the buffer that started as vals_b
-        k_gather_sorted<<<grid, 256, 0, s>>>(points, va, N, spts);
-        note_launch();
-    }
+    k_bin_init<<<1, 32, 0, s>>>(h, requested, d_total);
+    note_launch();
+    if ((e = (int)cudaMemsetAsync(cand_offsets, 0, ((size_t)P + 1) * 4, s))) return e;
     if (P > 0) {
-        k_poly_candidates<false><<<grid, 256, 0, s>>>(bb, po, P, h, cstart, spts, va,
-                                                      reinterpret_cast<unsigned *>(cand_offsets), nullptr,
-                                                      nullptr, 0, d_total);
+        k_poly_bbox<<<grid, 256, 0, s>>>(po, verts, P, bb, h);
+        k_bin_level<<<1, 32, 0, s>>>(h, L.lcap);
+        note_launch(2);
+        if ((e = (int)cudaMemsetAsync(ent, 0xff, (size_t)L.H * sizeof(CellEntry), s))) return e;
+        if ((e = (int)cudaMemsetAsync(cnt, 0, (size_t)L.H * 4, s))) return e;
+        k_cells<true><<<grid, 256, 0, s>>>(bb, po, P, h, ent, cnt, off, list_bb, list_id, big, L.hbits);
         note_launch();
+        if ((e = (int)cudaMemcpyAsync(off, cnt, (size_t)L.H * 4, cudaMemcpyDeviceToDevice, s))) return e;
+        if ((e = scan_exclusive(off, L.H, tmp, s))) return e;
+        k_cells<false><<<grid, 256, 0, s>>>(bb, po, P, h, ent, cnt, off, list_bb, list_id, big, L.hbits);
+        k_cells_pack<<<grid, 256, 0, s>>>(cnt, off, ent, L.H);
+        note_launch(2);
+        if (N > 0) {
+            k_probe_count<<<grid, PROBE_THREADS, 0, s>>>(points, N, h, ent, list_bb, list_id, big, bb, L.hbits,
+                                                         reinterpret_cast<unsigned *>(cand_offsets),
+                                                         reinterpret_cast<int2 *>(w + L.pairs), L.pcap, d_total);
+            note_launch();
+        }
         if ((e = scan_exclusive(reinterpret_cast<unsigned *>(cand_offsets), (long long)P + 1, tmp, s))) return e;
-    } else {
-        if ((e = (int)cudaMemsetAsync(cand_offsets, 0, 4, s))) return e;
     }
-    k_bin_finish<<<1, 32, 0, s>>>(h, d_total, cand_offsets, P, 0, nullptr);
+    k_bin_finish<<<1, 32, 0, s>>>(h, d_total, 0, nullptr);
     note_launch();
     return (int)cudaGetLastError();
 }
@@ -525,22 +639,32 @@ int launch_bin_fill(const int2 *points, long long N, const int32_t *po, const in
                     size_t ws_bytes, const int32_t *cand_offsets, int32_t *cand_ids, long long capacity,
                     int32_t *d_overflow, int n_sm, cudaStream_t s)
 {
+    (void)verts;
+    (void)po;
     const BinLayout L = bin_layout(N, P);
     if (ws_bytes < L.total) return (int)cudaErrorInvalidValue;
     char *w = static_cast<char *>(ws);
     BinHeader *h = reinterpret_cast<BinHeader *>(w + L.header);
     const int4 *bb = reinterpret_cast<const int4 *>(w + L.poly_bb);
-    // sorted ids after three passes: vals_b (odd number of swaps)
-    const int *sids = reinterpret_cast<const int *>(w + L.vals_b);
-    const int2 *spts = reinterpret_cast<const int2 *>(w + L.spts);
-    const unsigned *cstart = reinterpret_cast<const unsigned *>(w + L.cell_start);
+    const CellEntry *ent = reinterpret_cast<const CellEntry *>(w + L.ent);
+    const int4 *list_bb = reinterpret_cast<const int4 *>(w + L.list_bb);
+    const int *list_id = reinterpret_cast<const int *>(w + L.list_id);
+    const int *big = reinterpret_cast<const int *>(w + L.big);
+    unsigned *cursor = reinterpret_cast<unsigned *>(w + L.cursor);
+    int *long_list = reinterpret_cast<int *>(w + L.long_list);
     const int grid = n_sm * 8;
+    int e;
     if (P > 0 && N > 0) {
-        k_poly_candidates<true><<<grid, 256, 0, s>>>(bb, po, P, h, cstart, spts, sids, nullptr, cand_offsets,
-                                                     cand_ids, capacity, nullptr);
-        note_launch();
+        if ((e = (int)cudaMemsetAsync(cursor, 0, (size_t)P * 4, s))) return e;
+        if ((e = (int)cudaMemsetAsync(&h->n_long, 0, sizeof(int), s))) return e;
+        k_probe_fill<<<grid, PROBE_THREADS, 0, s>>>(points, N, h, ent, list_bb, list_id, big, bb, L.hbits,
+                                                    reinterpret_cast<const int2 *>(w + L.pairs), L.pcap,
+                                                    cand_offsets, cursor, cand_ids, capacity);
+        k_seg_sort<<<grid, 256, 0, s>>>(cand_offsets, P, cand_ids, capacity, h, long_list);
+        k_seg_sort_long<<<n_sm * 4, 256, 0, s>>>(cand_offsets, cand_ids, capacity, h, long_list);
+        note_launch(3);
     }
-    k_bin_finish<<<1, 32, 0, s>>>(h, nullptr, cand_offsets, P, capacity, d_overflow);
+    k_bin_finish<<<1, 32, 0, s>>>(h, nullptr, capacity, d_overflow);
     note_launch();
     return (int)cudaGetLastError();
 }

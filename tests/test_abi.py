@@ -96,10 +96,15 @@ def test_tuning_validation(lib):
 
 
 def test_bin_workspace_size_grows(lib):
+    """The binning workspace holds the polygons' boxes, cell table and lists (at least a 16-byte
+    box, two 8-byte slots and a list entry per polygon) and the recorded (polygon, point) pairs
+    (8 bytes for a quarter of the points)."""
     a = lib.pip_bin_workspace_bytes(1000, 10)
     b = lib.pip_bin_workspace_bytes(10_000_000, 100_000)
-    assert 0 < a < b
-    assert b >= 10_000_000 * (4 * 4 + 8)
+    c = lib.pip_bin_workspace_bytes(0, 100_000)
+    assert 0 < a < b and 0 < c < b
+    assert c >= 100_000 * (16 + 2 * 8 + 4)
+    assert b - c >= 10_000_000 // 4 * 8
 
 
 def test_argument_checks_of_the_other_entry_points(lib):

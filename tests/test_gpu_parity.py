@@ -244,6 +244,51 @@ def test_binning_is_deterministic(api):
     assert torch.equal(co1, co2) and torch.equal(ids1, ids2)
 
 
+def _bin_case(rng):
+    """Polygons that exercise every path of the binning: tiny boxes, boxes large enough to go on
+    the short list, empty polygons, and id lists long enough for each sort (warp registers,
+    warp shared memory, CTA shared memory, global memory)."""
+    polys = []
+    for _ in range(300):                      # tiny squares (a few points each)
+        x, y = rng.integers(-10**6, 10**6, 2)
+        s = int(rng.integers(50, 400))
+        polys.append(np.array([[x, y], [x + s, y], [x + s, y + s], [x, y + s]], dtype=np.int64))
+    hot = rng.integers(-10**6 + 50_000, 10**6 - 50_000, (2, 2))          # two hot spots of points
+    for (x, y), s in zip(hot, (3000, 16000)):                            # ~10^2 and ~10^3 points
+        polys.append(np.array([[x, y], [x + s, y], [x, y + s]], dtype=np.int64))
+    polys.append(np.zeros((0, 2), dtype=np.int64))                      # empty polygon
+    big = 2 * 10**6
+    polys.append(np.array([[-big, -big], [big, -big], [0, big]], dtype=np.int64))   # covers everything
+    for i in range(300):                      # many wide, flat boxes: the short list fills up
+        y = -10**6 + 6000 * i
+        polys.append(np.array([[-10**6, y], [10**6, y], [0, y + 40]], dtype=np.int64))
+    po = np.zeros(len(polys) + 1, dtype=np.int64)
+    po[1:] = np.cumsum([len(q) for q in polys])
+    verts = np.concatenate(polys).astype(np.int32)
+    pts = rng.integers(-10**6, 10**6, (300_000, 2)).astype(np.int32)
+    extra = [(c + rng.integers(-20_000, 20_000, (30_000, 2))) for c in hot]
+    pts = np.concatenate([pts] + [e.astype(np.int32) for e in extra])
+    return pts, po.astype(np.int32), verts
+
+
+@pytest.mark.parametrize("cell_size", [0, 1, 1 << 12, 1 << 20])
+def test_binning_paths_and_cell_sizes(api, cell_size):
+    """Every candidate list equals the oracle's closed-box list exactly (ids ascending), for the
+    automatic cell size and for requested ones from one unit (raised to what the pair list
+    holds) to a quarter of the domain."""
+    rng = np.random.default_rng(77)
+    pts, po, verts = _bin_case(rng)
+    P = len(po) - 1
+    d_pts, d_po, d_v = (torch.from_numpy(x).cuda() for x in (pts, po, verts))
+    co, ids = api.bin_join(d_pts, d_po, d_v, cell_size=cell_size)
+    torch.cuda.synchronize()
+    counts, want_ids = oracle.bbox_join(pts, po, verts, np.arange(P))
+    assert counts.max() > 8192 and ((counts > 1024) & (counts <= 8192)).any()
+    assert ((counts > 32) & (counts <= 1024)).any()
+    assert np.array_equal(np.diff(co.cpu().numpy().astype(np.int64)), counts)
+    assert np.array_equal(ids.cpu().numpy(), want_ids)
+
+
 def _concat(ws, name):
     """Concatenate CSR workloads (polygons, points and candidate lists) into one."""
     pts, po, vs, co, ids = [], [0], [], [0], []
