@@ -305,18 +305,20 @@ def run_join(args, rank, world):
     host_pts = [W.join_points(clusters, seed + 1000 + b, n_pts) for b in range(nb)]
     d_pts = [torch.from_numpy(x).cuda() for x in host_pts]
     stream = torch.cuda.Stream()
-    # independent batches run on several streams (each with its own binning workspace) so that
-    # their latency-bound kernels overlap; the graph forks from and joins back to `stream`
+    # a step builds the polygon index once; the batches then probe it on several streams (each
+    # with its own probe workspace) so that their latency-bound kernels overlap; the graph forks
+    # from and joins back to `stream`
     ns = max(1, min(args.streams, nb))
     streams = [torch.cuda.Stream() for _ in range(ns)]
-    wss = [api.bin_workspace(n_pts, P) for _ in range(ns)]
-    ws = wss[0]
+    index = api.bin_index(d_po, d_v, stream=stream)
+    probes = [api.probe_workspace(n_pts, P) for _ in range(ns)]
     co = [torch.empty(P + 1, dtype=torch.int32, device="cuda") for _ in range(nb)]
     tot = [torch.empty(1, dtype=torch.int64, device="cuda") for _ in range(nb)]
     with torch.cuda.stream(stream):
         totals = []
         for b in range(nb):
-            api.pip_bin_count(d_pts[b], d_po, d_v, workspace=ws, cand_offsets=co[b], d_total=tot[b], stream=stream)
+            api.pip_bin_probe_count(d_pts[b], index, P, probe=probes[0], cand_offsets=co[b], d_total=tot[b],
+                                    stream=stream)
             stream.synchronize()
             totals.append(int(tot[b].item()))
     cap = int(max(totals) * 1.1) + 1024
@@ -325,12 +327,13 @@ def run_join(args, rank, world):
     ovf = torch.zeros(nb, dtype=torch.int32, device="cuda")
 
     def one_pass(classify=True):
+        api.bin_index(d_po, d_v, index=index, stream=stream)
         for s_ in streams:
             s_.wait_stream(stream)
         for b in range(nb):
-            s_, w_ = streams[b % ns], wss[b % ns]
-            api.pip_bin_count(d_pts[b], d_po, d_v, workspace=w_, cand_offsets=co[b], d_total=tot[b], stream=s_)
-            api.pip_bin_fill(d_pts[b], d_po, d_v, w_, co[b], ids[b], d_overflow=ovf[b:b + 1], stream=s_)
+            s_, q_ = streams[b % ns], probes[b % ns]
+            api.pip_bin_probe_count(d_pts[b], index, P, probe=q_, cand_offsets=co[b], d_total=tot[b], stream=s_)
+            api.pip_bin_probe_fill(d_pts[b], index, P, q_, co[b], ids[b], d_overflow=ovf[b:b + 1], stream=s_)
             if classify:
                 api.pip_classify(d_pts[b], d_po, d_v, co[b], ids[b], out=outs[b], stream=s_)
         for s_ in streams:
@@ -381,13 +384,13 @@ def run_join(args, rank, world):
     ms, clocks = res["full"]
     T_all = sum_over_ranks(dist, T)
     bin_ms = res["binning"][0]
-    # algorithmic bytes of a step: per batch, binning reads the points twice (bounds, keys) and
-    # gathers them once in cell order, sorts (key, id) pairs in three radix passes (read and
-    # write 8 B each), reads the polygons' vertices for their boxes and writes the CSR; the
-    # classification reads vertices, offsets, ids and points and writes the bits
+    # algorithmic bytes of a step (what any binning + classification must move, independent of
+    # how it is done): the polygons' vertices read once for the index; per batch the points read
+    # once and the CSR written (offsets, ids); the classification reads vertices, offsets, ids
+    # and points and writes the bits
     V = int(po[-1])
     classify_bytes = 8 * V * nb + 8 * (P + 1) * nb + 12 * C + C // 8
-    bin_bytes = nb * (3 * 8 * n_pts + 3 * 2 * 8 * n_pts + 8 * V + 4 * (P + 1)) + 4 * C
+    bin_bytes = 8 * V + nb * (8 * n_pts + 4 * (P + 1)) + 4 * C
     join_bytes = classify_bytes + bin_bytes
     peaks, peak_kind = measured_peaks()
     hbm = float(peaks["hbm_gbs"])

@@ -40,7 +40,8 @@
  * and never synchronise it; they check host-visible arguments only (NULL, sizes,
  * alignment) and return PIP_OK or a negative PIP_ERR_* code without launching anything.
  * The contents of device arrays (monotone offsets, ids in range) are checked only by
- * pip_validate.  The library owns a small per-device workspace (work counters and
+ * pip_validate; the classify kernels never read a point through an id outside
+ * [0, n_points) (such a candidate gets bit 0).  The library owns a small per-device workspace (work counters and
  * statistics), created on the first call made outside stream capture; a call made during
  * capture before the workspace exists returns PIP_ERR_WORKSPACE.  Calls on different
  * streams that overlap on the GPU share the statistics counters only.
@@ -205,23 +206,47 @@ int pip_quantize_lonlat(const double *lonlat, int64_t n_values, double scale, in
 
 /*
  * Uniform-grid binning (not in the paper; it builds the candidate CSR of a spatial join):
- * candidates of polygon k = every point inside k's CLOSED bounding box, listed in a fixed
- * order (grid cells row-major over the box, ascending point id within a cell), so that
- * repeated calls on the same data give identical arrays.
+ * candidates of polygon k = every point inside k's CLOSED bounding box, listed by ascending
+ * point id, so that repeated calls on the same data give identical arrays.  The polygons, not
+ * the points, are binned: a polygon index (their boxes in a hash table of square cells of edge
+ * 2^l, l the finest level at which the boxes' cells fit a list of 4 entries per polygon + 1024,
+ * boxes of more than 64 cells on a short list of at most 256 that every point tests) is built
+ * once and then probed by each batch of points.  cand_offsets is int32: the candidate total
+ * must stay below 2^31 (*d_total reports it in int64 regardless).
  *
- * pip_bin_workspace_bytes returns the size of the caller-owned scratch buffer that both
- * binning calls need for n_points points and n_polys polygons.
+ * Two-step form (one index, any number of batches, concurrently on several streams when each
+ * has its own probe workspace):
+ *   pip_bin_index_bytes(n_polys) / pip_bin_index: builds the index (device buffer `index`,
+ *     caller-owned, 16-byte aligned) of the polygons; cell_size > 0 asks for cells of at least
+ *     that many units (rounded up to a power of two, coarser if the list needs it), 0 = finest.
+ *   pip_bin_probe_bytes(n_points, n_polys): size of a batch's probe workspace.
+ *   pip_bin_probe_count: writes cand_offsets [n_polys + 1] (device, exclusive prefix sum of
+ *     the per-polygon counts) and *d_total (device int64) = the number of candidates, and keeps
+ *     the batch's (polygon, point) pairs in the probe workspace (up to n_points / 2 + 1024;
+ *     beyond that the fill pass probes the points again).
+ *   pip_bin_probe_fill: writes cand_ids (device, capacity `capacity` ids) for the same points,
+ *     index and probe workspace.  If the total exceeds `capacity`, ids past the capacity are
+ *     dropped and *d_overflow (device int32, may be NULL) is set to 1; otherwise 0.
+ * A probe of an index that was not built (or was built for another polygon count) finds no
+ * candidates.  n_polys is the indexed polygon count.
  *
- * pip_bin_count: bins the points (cell size `cell_size` units; 0 = chosen on the device
- * from the mean polygon extent, capped so that the grid has at most 2^24 cells), then
- * writes cand_offsets [n_polys + 1] (device, exclusive prefix sum of the per-polygon
- * counts) and *d_total (device int64) = the number of candidates.  The grid stays in the
- * workspace for pip_bin_fill.
- *
- * pip_bin_fill: writes cand_ids (device, capacity `capacity` ids) from the same inputs and
- * workspace.  If the total exceeds `capacity`, ids past the capacity are dropped and
- * *d_overflow (device int32, may be NULL) is set to 1; otherwise it is set to 0.
+ * One-step form: pip_bin_workspace_bytes(n_points, n_polys) = index + one probe workspace;
+ * pip_bin_count builds the index and runs the count pass, pip_bin_fill the fill pass, on one
+ * workspace (same points and polygons in both calls).
  */
+size_t pip_bin_index_bytes(int32_t n_polys);
+int pip_bin_index(const int32_t *poly_offsets, const int32_t *verts, int32_t n_polys,
+                  int32_t cell_size, void *index, size_t index_bytes, void *stream);
+size_t pip_bin_probe_bytes(int64_t n_points, int32_t n_polys);
+int pip_bin_probe_count(const int32_t *points, int64_t n_points,
+                        const void *index, size_t index_bytes, int32_t n_polys,
+                        void *probe, size_t probe_bytes,
+                        int32_t *cand_offsets, int64_t *d_total, void *stream);
+int pip_bin_probe_fill(const int32_t *points, int64_t n_points,
+                       const void *index, size_t index_bytes, int32_t n_polys,
+                       void *probe, size_t probe_bytes,
+                       const int32_t *cand_offsets, int32_t *cand_ids, int64_t capacity,
+                       int32_t *d_overflow, void *stream);
 size_t pip_bin_workspace_bytes(int64_t n_points, int32_t n_polys);
 int pip_bin_count(const int32_t *points, int64_t n_points,
                   const int32_t *poly_offsets, const int32_t *verts, int32_t n_polys,

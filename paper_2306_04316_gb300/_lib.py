@@ -61,6 +61,12 @@ _SIGS = {
     "pip_quantize_lonlat": ([_P, _I64, ctypes.c_double, _P, _P, _P], ctypes.c_int),
     "pip_slab_build": ([_P, _P, _I32, _I64, _I32, _P, ctypes.c_size_t, _P, _P], ctypes.c_int),
     "pip_bin_workspace_bytes": ([_I64, _I32], ctypes.c_size_t),
+    "pip_bin_index_bytes": ([_I32], ctypes.c_size_t),
+    "pip_bin_index": ([_P, _P, _I32, _I32, _P, ctypes.c_size_t, _P], ctypes.c_int),
+    "pip_bin_probe_bytes": ([_I64, _I32], ctypes.c_size_t),
+    "pip_bin_probe_count": ([_P, _I64, _P, ctypes.c_size_t, _I32, _P, ctypes.c_size_t, _P, _P, _P], ctypes.c_int),
+    "pip_bin_probe_fill": ([_P, _I64, _P, ctypes.c_size_t, _I32, _P, ctypes.c_size_t, _P, _P, _I64, _P, _P],
+                           ctypes.c_int),
     "pip_bin_count": ([_P, _I64, _P, _P, _I32, _I32, _P, ctypes.c_size_t, _P, _P, _P], ctypes.c_int),
     "pip_bin_fill": ([_P, _I64, _P, _P, _I32, _P, ctypes.c_size_t, _P, _P, _I64, _P, _P], ctypes.c_int),
     "pip_set_tuning": ([_I32, _I32, _I32], ctypes.c_int),

@@ -195,6 +195,53 @@ def pip_bin_fill(points, poly_offsets, verts, workspace, cand_offsets, cand_ids,
     return cand_ids
 
 
+def bin_index(poly_offsets, verts, cell_size=0, index=None, stream=None):
+    """Polygon index of the binning (build once, probe with any number of point batches)."""
+    lib = _lib.load()
+    _need(poly_offsets, "poly_offsets")
+    _need(verts, "verts", 2)
+    n_polys = int(poly_offsets.shape[0]) - 1
+    if index is None:
+        index = torch.empty(int(lib.pip_bin_index_bytes(n_polys)), dtype=torch.uint8, device=verts.device)
+    rc = lib.pip_bin_index(_ptr(poly_offsets), _ptr(verts), n_polys, int(cell_size), _ptr(index), index.numel(),
+                           _stream(stream))
+    _lib.check("pip_bin_index", rc)
+    return index
+
+
+def probe_workspace(n_points: int, n_polys: int, device="cuda"):
+    lib = _lib.load()
+    return torch.empty(int(lib.pip_bin_probe_bytes(n_points, n_polys)), dtype=torch.uint8, device=device)
+
+
+def pip_bin_probe_count(points, index, n_polys, probe=None, cand_offsets=None, d_total=None, stream=None):
+    """Count pass of one batch against a polygon index: returns (cand_offsets, d_total, probe)."""
+    lib = _lib.load()
+    _need(points, "points", 2)
+    n_points = int(points.shape[0])
+    if probe is None:
+        probe = probe_workspace(n_points, n_polys, points.device)
+    if cand_offsets is None:
+        cand_offsets = torch.empty(n_polys + 1, dtype=torch.int32, device=points.device)
+    if d_total is None:
+        d_total = torch.empty(1, dtype=torch.int64, device=points.device)
+    rc = lib.pip_bin_probe_count(_ptr(points), n_points, _ptr(index), index.numel(), int(n_polys), _ptr(probe),
+                                 probe.numel(), _ptr(cand_offsets), _ptr(d_total), _stream(stream))
+    _lib.check("pip_bin_probe_count", rc)
+    return cand_offsets, d_total, probe
+
+
+def pip_bin_probe_fill(points, index, n_polys, probe, cand_offsets, cand_ids, d_overflow=None, stream=None):
+    """Fill pass of one batch (after its count pass on the same probe workspace)."""
+    lib = _lib.load()
+    n_points = int(points.shape[0])
+    rc = lib.pip_bin_probe_fill(_ptr(points), n_points, _ptr(index), index.numel(), int(n_polys), _ptr(probe),
+                                probe.numel(), _ptr(cand_offsets), _ptr(cand_ids), int(cand_ids.numel()),
+                                _ptr(d_overflow), _stream(stream))
+    _lib.check("pip_bin_probe_fill", rc)
+    return cand_ids
+
+
 def bin_join(points, poly_offsets, verts, cell_size=0, stream=None):
     """Both binning passes with one host read of the candidate total in between."""
     co, tot, ws = pip_bin_count(points, poly_offsets, verts, cell_size, stream=stream)

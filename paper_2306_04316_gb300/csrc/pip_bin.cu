@@ -4,7 +4,10 @@
 // the pre-pass that feeds the batched classify kernel.  Candidates of polygon k are all points
 // inside k's CLOSED bounding box -- a necessary condition for being inside k, so no inside
 // point is ever dropped.  The polygons are binned, not the points, so no pass ever sorts the
-// points.  Steps, all on the device, no host synchronisation:
+// points: steps 1-3 build a polygon index (pip_bin_index, once per polygon set), steps 4-5
+// probe it with a batch of points (pip_bin_probe_count / pip_bin_probe_fill; several batches
+// may probe one index at once, each with its own probe workspace).  pip_bin_count and
+// pip_bin_fill run both on one workspace.  All on the device, no host synchronisation:
 //   1. polygon bounding boxes (one warp per polygon); lane l of the warp also counts the cells
 //      of edge 2^l that the box covers, for every level l at once;
 //   2. the level (one thread): the finest cell edge 2^l at which the (polygon, cell) pairs of
@@ -15,14 +18,14 @@
 //      (each entry a copy of the polygon's box, so that a point reads its cell's slot -- key,
 //      first entry and count in 16 bytes -- and then one contiguous run of boxes);
 //   4. per point (one thread): its cell's polygons and the short list, each box tested; the
-//      count pass (pip_bin_count) counts per polygon with atomics, scans the counts into
-//      cand_offsets and records the (polygon, point) pairs in the workspace; the fill pass
-//      (pip_bin_fill) places each recorded id by an atomic cursor (probing the points again
-//      only if more pairs were found than the workspace records: N / 4 + 4 per polygon);
-//   5. every polygon's id list sorted ascending (bitonic: one warp per polygon in its registers
-//      up to 32 ids or its shared memory up to 1024; longer lists queued for one CTA each, in
-//      shared memory up to 8192, else in place in global memory), so that the CSR is the same
-//      on every run.
+//      count pass counts per polygon with atomics, scans the counts into cand_offsets and
+//      records the (polygon, point) pairs in the probe workspace; the fill pass places each
+//      recorded id by an atomic cursor (probing the points again only if more pairs were found
+//      than the workspace records: N / 2 + 1024);
+//   5. every polygon's id list sorted ascending (bitonic: one lane per polygon in its registers
+//      up to 16 ids; longer lists queued for one warp each, in its registers up to 32 or its
+//      shared memory up to 1024, or for one CTA each, in shared memory up to 8192, else in place
+//      in global memory), so that the CSR is the same on every run.
 #include <algorithm>
 
 #include "pip_device.cuh"
@@ -34,26 +37,41 @@ constexpr int BIN_CELL_CAP = 64;       // boxes covering more cells than this go
 constexpr int BIN_BIG_CAP = 256;       // most polygons on the short list
 constexpr unsigned long long BIN_EMPTY = ~0ull;   // an empty hash slot (cx < 2^31 for level >= 1)
 constexpr int SCAN_TILE = 1024;        // elements per scan block (256 threads x 4)
+constexpr int SORT_LANE = 16;          // ids a lane sorts in its registers
 constexpr int SORT_WARP_SMEM = 1024;   // ids a warp sorts in its own shared memory
 constexpr int SORT_CTA_SMEM = 8192;    // ids a CTA sorts in shared memory
 
-struct BinHeader {
+constexpr unsigned INDEX_MAGIC = 0x50495849u;   // a polygon index whose build has completed
+
+// The polygon index: built once per polygon set, read-only while batches of points probe it.
+struct IndexHeader {
     unsigned long long cells[32];    // cells[l]: (polygon, cell) pairs of the boxes with <= BIN_CELL_CAP cells
     unsigned long long big[32];      // big[l]: boxes with more cells than that, at cell edge 2^l
     int level;                       // chosen cell edge 2^level
     int n_big;                       // polygons on the short list
     int requested_level;             // 0: automatic
-    int n_long;                      // id lists queued for the CTA-wide sort
-    long long total;                 // candidates (int64)
-    unsigned long long n_pairs;      // (polygon, point) pairs the count pass recorded
+    int n_polys;                     // polygons indexed
+    unsigned magic;                  // INDEX_MAGIC once the build has completed
+    int pad[3];
 };
 
-// Workspace layout (offsets in bytes, each 256-aligned).  Only the polygon count sizes it.
-struct BinLayout {
-    size_t header, poly_bb, ent, cnt, off, list_bb, list_id, big, cursor, long_list, pairs, scan_tmp, total;
+// State of one batch's probe passes.
+struct ProbeHeader {
+    long long total;                 // candidates (int64)
+    unsigned long long n_pairs;      // (polygon, point) pairs the count pass recorded
+    int n_long;                      // id lists queued for the CTA-wide sort
+    int n_medium;                    // id lists queued for the warp-wide sort
+};
+
+// Layouts (offsets in bytes, each 256-aligned).  The index is sized by the polygon count only.
+struct IndexLayout {
+    size_t header, poly_bb, ent, cnt, off, list_bb, list_id, big, scan_tmp, total;
     long long H, lcap;               // hash slots (a power of two), pair-list capacity
-    long long pcap;                  // (polygon, point) pairs the count pass can record
     int hbits;
+};
+struct ProbeLayout {
+    size_t header, cursor, medium_list, long_list, pairs, scan_tmp, total;
+    long long pcap;                  // (polygon, point) pairs the count pass can record
 };
 
 // A slot of the cell table: the cell's key, then (first list entry, polygons) once built.
@@ -76,17 +94,15 @@ long long scan_tmp_elems(long long n)
     return t + 1;
 }
 
-static BinLayout bin_layout(long long N, int P)
+static IndexLayout index_layout(int P)
 {
-    BinLayout L;
-    L.pcap = N / 4 + 4LL * P + 1024;
+    IndexLayout L;
     L.lcap = pair_capacity(P);
     L.hbits = 1;
     while ((1LL << L.hbits) < 4 * L.lcap) ++L.hbits;   // at most a quarter full
     L.H = 1LL << L.hbits;
-    const long long scan_max = std::max<long long>(L.H, (long long)P + 1);
     size_t o = 0;
-    L.header = o; o += align256(sizeof(BinHeader));
+    L.header = o; o += align256(sizeof(IndexHeader));
     L.poly_bb = o; o += align256((size_t)std::max(P, 1) * 16);
     L.ent = o; o += align256((size_t)L.H * sizeof(CellEntry));
     L.cnt = o; o += align256((size_t)L.H * 4);
@@ -94,15 +110,33 @@ static BinLayout bin_layout(long long N, int P)
     L.list_bb = o; o += align256((size_t)L.lcap * 16);
     L.list_id = o; o += align256((size_t)L.lcap * 4);
     L.big = o; o += align256((size_t)BIN_BIG_CAP * 4);
-    L.cursor = o; o += align256((size_t)std::max(P, 1) * 4);
-    L.long_list = o; o += align256((size_t)std::max(P, 1) * 4);
-    L.pairs = o; o += align256((size_t)L.pcap * 8);
-    L.scan_tmp = o; o += align256((size_t)scan_tmp_elems(scan_max) * 4);
+    L.scan_tmp = o; o += align256((size_t)scan_tmp_elems(L.H) * 4);
     L.total = o;
     return L;
 }
 
-size_t bin_workspace_bytes(long long n_points, int n_polys) { return bin_layout(n_points, n_polys).total; }
+static ProbeLayout probe_layout(long long N, int P)
+{
+    ProbeLayout L;
+    L.pcap = N / 2 + 1024;
+    size_t o = 0;
+    L.header = o; o += align256(sizeof(ProbeHeader));
+    L.cursor = o; o += align256((size_t)std::max(P, 1) * 4);
+    L.medium_list = o; o += align256((size_t)std::max(P, 1) * 4);
+    L.long_list = o; o += align256((size_t)std::max(P, 1) * 4);
+    L.pairs = o; o += align256((size_t)L.pcap * 8);
+    L.scan_tmp = o; o += align256((size_t)scan_tmp_elems((long long)P + 1) * 4);
+    L.total = o;
+    return L;
+}
+
+size_t bin_index_bytes(int n_polys) { return index_layout(n_polys).total; }
+size_t bin_probe_bytes(long long n_points, int n_polys) { return probe_layout(n_points, n_polys).total; }
+// pip_bin_count / pip_bin_fill: the index, then one probe workspace
+size_t bin_workspace_bytes(long long n_points, int n_polys)
+{
+    return bin_index_bytes(n_polys) + bin_probe_bytes(n_points, n_polys);
+}
 
 // ------------------------------------------------------------------------------------------
 // exclusive scan of uint32 (in place, multi-level)
@@ -173,7 +207,7 @@ int scan_exclusive(unsigned *d, long long n, unsigned *tmp, cudaStream_t s)
 // ------------------------------------------------------------------------------------------
 // polygon boxes and the level
 // ------------------------------------------------------------------------------------------
-__global__ void k_bin_init(BinHeader *h, int requested_level, long long *d_total)
+__global__ void k_index_init(IndexHeader *h, int requested_level, int P)
 {
     const int t = threadIdx.x;
     if (blockIdx.x == 0 && t < 32) {
@@ -183,11 +217,32 @@ __global__ void k_bin_init(BinHeader *h, int requested_level, long long *d_total
             h->level = 31;
             h->n_big = 0;
             h->requested_level = requested_level;
-            h->total = 0;
-            h->n_pairs = 0;
-            if (d_total) *d_total = 0;
+            h->n_polys = P;
+            h->magic = 0;
         }
     }
+}
+
+__global__ void k_index_finish(IndexHeader *h)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0) h->magic = INDEX_MAGIC;
+}
+
+__global__ void k_probe_init(ProbeHeader *q, long long *d_total)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        q->total = 0;
+        q->n_pairs = 0;
+        q->n_long = 0;
+        q->n_medium = 0;
+        if (d_total) *d_total = 0;
+    }
+}
+
+// the index was built, for this many polygons
+__device__ __forceinline__ bool index_ok(const IndexHeader *h, int P)
+{
+    return h->magic == INDEX_MAGIC && h->n_polys == P;
 }
 
 // cell coordinate of x at level l: (x + 2^31) >> l
@@ -204,7 +259,7 @@ __device__ __forceinline__ unsigned long long hash_slot(unsigned long long key, 
 }
 
 __global__ void k_poly_bbox(const int32_t *__restrict__ po, const int2 *__restrict__ verts, int P, int4 *bb,
-                            BinHeader *h)
+                            IndexHeader *h)
 {
     const int lane = threadIdx.x & 31;
     const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -250,7 +305,7 @@ __global__ void k_poly_bbox(const int32_t *__restrict__ po, const int2 *__restri
 
 // The finest level at or above the requested one whose pairs fit the list and whose larger boxes
 // fit the short list.  Level 31 always qualifies: every box covers at most 2 x 2 cells.
-__global__ void k_bin_level(BinHeader *h, long long lcap)
+__global__ void k_bin_level(IndexHeader *h, long long lcap)
 {
     if (blockIdx.x != 0 || threadIdx.x >= 32) return;
     const int l = threadIdx.x;
@@ -266,7 +321,7 @@ __global__ void k_bin_level(BinHeader *h, long long lcap)
 // INSERT: claim every covered cell's slot and count the polygon there; else find the slot and
 // append the polygon to the cell's list.  Boxes with too many cells go on the short list.
 template <bool INSERT>
-__global__ void k_cells(const int4 *__restrict__ bb, const int32_t *__restrict__ po, int P, BinHeader *h,
+__global__ void k_cells(const int4 *__restrict__ bb, const int32_t *__restrict__ po, int P, IndexHeader *h,
                         CellEntry *ent, unsigned *cnt, unsigned *off, int4 *list_bb, int *list_id, int *big,
                         int hbits)
 {
@@ -356,11 +411,13 @@ __device__ __forceinline__ void probe_point(int2 p, long long i, int l, unsigned
 // for the fill pass -- staged per warp in shared memory and appended with one atomic per flush,
 // in any order (the fill's sort fixes the order); pairs past the capacity are dropped and the
 // fill pass then probes the points again.  Warps run on their own: no CTA barrier.
-__global__ void __launch_bounds__(PROBE_THREADS) k_probe_count(
-    const int2 *__restrict__ pts, long long N, BinHeader *h, const CellEntry *__restrict__ ent,
-    const int4 *__restrict__ list_bb, const int *__restrict__ list_id, const int *__restrict__ big,
-    const int4 *__restrict__ bb, int hbits, unsigned *counts, int2 *pairs, long long pcap, long long *d_total)
+__global__ void __launch_bounds__(PROBE_THREADS, 8) k_probe_count(
+    const int2 *__restrict__ pts, long long N, const IndexHeader *__restrict__ h, int P, ProbeHeader *q,
+    const CellEntry *__restrict__ ent, const int4 *__restrict__ list_bb, const int *__restrict__ list_id,
+    const int *__restrict__ big, const int4 *__restrict__ bb, int hbits, unsigned *counts, int2 *pairs,
+    long long pcap, long long *d_total)
 {
+    if (!index_ok(h, P)) return;
     constexpr int WS = PROBE_STAGE / (PROBE_THREADS / 32);   // a warp's stage
     __shared__ int2 s_pair[PROBE_STAGE];
     __shared__ int s_n[PROBE_THREADS / 32];
@@ -377,7 +434,7 @@ __global__ void __launch_bounds__(PROBE_THREADS) k_probe_count(
         if (j < WS) {
             stage[j] = make_int2(k, (int)i);
         } else {   // the stage is full: straight to the global list
-            const unsigned long long g = atomicAdd(&h->n_pairs, 1ull);
+            const unsigned long long g = atomicAdd(&q->n_pairs, 1ull);
             if (g < (unsigned long long)pcap) pairs[g] = make_int2(k, (int)i);
         }
     };
@@ -385,7 +442,7 @@ __global__ void __launch_bounds__(PROBE_THREADS) k_probe_count(
         __syncwarp();
         const int n = min(s_n[w], WS);
         unsigned long long b = 0;
-        if (lane == 0 && n) b = atomicAdd(&h->n_pairs, (unsigned long long)n);
+        if (lane == 0 && n) b = atomicAdd(&q->n_pairs, (unsigned long long)n);
         b = __shfl_sync(FULL, b, 0);
         for (int j = lane; j < n; j += 32)
             if (b + j < (unsigned long long)pcap) pairs[b + j] = stage[j];
@@ -411,17 +468,19 @@ __global__ void __launch_bounds__(PROBE_THREADS) k_probe_count(
 
 // Fill pass: every id placed at its polygon's offset plus an atomic cursor -- from the pairs the
 // count pass recorded, or, when they did not all fit, by probing the points again.
-__global__ void __launch_bounds__(PROBE_THREADS) k_probe_fill(
-    const int2 *__restrict__ pts, long long N, const BinHeader *__restrict__ h, const CellEntry *__restrict__ ent,
-    const int4 *__restrict__ list_bb, const int *__restrict__ list_id, const int *__restrict__ big,
-    const int4 *__restrict__ bb, int hbits, const int2 *__restrict__ pairs, long long pcap,
-    const int32_t *__restrict__ cand_offsets, unsigned *cursor, int32_t *cand_ids, long long capacity)
+__global__ void __launch_bounds__(PROBE_THREADS, 8) k_probe_fill(
+    const int2 *__restrict__ pts, long long N, const IndexHeader *__restrict__ h, int P,
+    const ProbeHeader *__restrict__ q, const CellEntry *__restrict__ ent, const int4 *__restrict__ list_bb,
+    const int *__restrict__ list_id, const int *__restrict__ big, const int4 *__restrict__ bb, int hbits,
+    const int2 *__restrict__ pairs, long long pcap, const int32_t *__restrict__ cand_offsets, unsigned *cursor,
+    int32_t *cand_ids, long long capacity)
 {
+    if (!index_ok(h, P)) return;
     auto place = [&](int k, long long i) {
         const long long pos = (long long)__ldg(cand_offsets + k) + atomicAdd(cursor + k, 1u);
         if (pos < capacity) cand_ids[pos] = (int32_t)i;
     };
-    const unsigned long long np = h->n_pairs;
+    const unsigned long long np = q->n_pairs;
     const long long t0 = (long long)blockIdx.x * blockDim.x + threadIdx.x, nt = (long long)gridDim.x * blockDim.x;
     if (np <= (unsigned long long)pcap) {
         for (long long j = t0; j < (long long)np; j += nt) {
@@ -485,34 +544,32 @@ __device__ void bitonic_sort(int *V, int n, int t0, int nt, Sync sync)
     }
 }
 
-// One warp per 32 consecutive polygons: lists of up to 8 ids sorted by their own lane in
-// registers, lists of up to SORT_WARP_SMEM ids by the whole warp (in registers up to 32, else
-// in its shared memory); longer lists are queued for k_seg_sort_long.
+// One lane per polygon: lists of up to SORT_LANE ids sorted in the lane's registers; longer ones
+// queued, up to SORT_WARP_SMEM ids for k_seg_sort_medium (a warp each), beyond for
+// k_seg_sort_long (a CTA each).
 __global__ void __launch_bounds__(256) k_seg_sort(const int32_t *__restrict__ cand_offsets, int P, int32_t *ids,
-                                                  long long capacity, BinHeader *h, int *long_list)
+                                                  long long capacity, ProbeHeader *h, int *medium_list,
+                                                  int *long_list)
 {
-    __shared__ int s_v[8 * SORT_WARP_SMEM];
     const int lane = threadIdx.x & 31;
-    int *wv = s_v + (threadIdx.x >> 5) * SORT_WARP_SMEM;
-    const long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
-    for (long long k0 = gw * 32; k0 < P; k0 += nw * 32) {
-        const long long kl = k0 + lane;
-        long long my_a = 0, my_n = 0;
-        if (kl < P) {
-            my_a = min((long long)cand_offsets[kl], capacity);
-            my_n = min((long long)cand_offsets[kl + 1], capacity) - my_a;
+    for (long long k0 = (long long)blockIdx.x * blockDim.x + threadIdx.x - lane; k0 < P;
+         k0 += (long long)gridDim.x * blockDim.x) {
+        const long long k = k0 + lane;   // k0: the warp's first polygon
+        long long a = 0, n = 0;
+        if (k < P) {
+            a = min((long long)cand_offsets[k], capacity);
+            n = min((long long)cand_offsets[k + 1], capacity) - a;
         }
-        if (my_n > 1 && my_n <= 8) {
-            int v[8];
+        if (n > 1 && n <= SORT_LANE) {
+            int v[SORT_LANE];
             #pragma unroll
-            for (int i = 0; i < 8; ++i) v[i] = i < my_n ? ids[my_a + i] : INT_MAX;
+            for (int i = 0; i < SORT_LANE; ++i) v[i] = i < n ? ids[a + i] : INT_MAX;
             #pragma unroll
-            for (int kk = 2; kk <= 8; kk <<= 1) {
+            for (int kk = 2; kk <= SORT_LANE; kk <<= 1) {
                 #pragma unroll
                 for (int j = kk >> 1; j > 0; j >>= 1) {
                     #pragma unroll
-                    for (int i = 0; i < 8; ++i) {
+                    for (int i = 0; i < SORT_LANE; ++i) {
                         const int q = j == (kk >> 1) ? (i ^ (kk - 1)) : (i ^ j);
                         if (q > i) {
                             const int x = min(v[i], v[q]), y = max(v[i], v[q]);
@@ -523,25 +580,51 @@ __global__ void __launch_bounds__(256) k_seg_sort(const int32_t *__restrict__ ca
                 }
             }
             #pragma unroll
-            for (int i = 0; i < 8; ++i)
-                if (i < my_n) ids[my_a + i] = v[i];
+            for (int i = 0; i < SORT_LANE; ++i)
+                if (i < n) ids[a + i] = v[i];
         }
-        for (unsigned m = __ballot_sync(FULL, my_n > 8); m; m &= m - 1) {
-            const int src = __ffs(m) - 1;
-            const long long a = __shfl_sync(FULL, my_a, src), n = __shfl_sync(FULL, my_n, src);
-            if (n <= 32) {
-                int v = lane < n ? ids[a + lane] : INT_MAX;
-                v = warp_sort32(v, lane);
-                if (lane < n) ids[a + lane] = v;
-            } else if (n <= SORT_WARP_SMEM) {
-                for (int i = lane; i < n; i += 32) wv[i] = ids[a + i];
-                __syncwarp();
-                bitonic_sort(wv, (int)n, lane, 32, [] { __syncwarp(); });
-                for (int i = lane; i < n; i += 32) ids[a + i] = wv[i];
-                __syncwarp();
-            } else if (lane == 0) {
-                long_list[atomicAdd(&h->n_long, 1)] = (int)(k0 + src);
-            }
+        // queue the longer lists, one atomic per warp and queue
+        const bool med = n > SORT_LANE && n <= SORT_WARP_SMEM, lng = n > SORT_WARP_SMEM;
+        const unsigned mm = __ballot_sync(FULL, med), ml = __ballot_sync(FULL, lng);
+        int bm = 0, bl = 0;
+        if (lane == 0) {
+            if (mm) bm = atomicAdd(&h->n_medium, __popc(mm));
+            if (ml) bl = atomicAdd(&h->n_long, __popc(ml));
+        }
+        bm = __shfl_sync(FULL, bm, 0);
+        bl = __shfl_sync(FULL, bl, 0);
+        const unsigned below = (1u << lane) - 1u;
+        if (med) medium_list[bm + __popc(mm & below)] = (int)k;
+        if (lng) long_list[bl + __popc(ml & below)] = (int)k;
+    }
+}
+
+// The queued lists of up to SORT_WARP_SMEM ids, one warp each: in registers up to 32, else in
+// the warp's shared memory.
+__global__ void __launch_bounds__(256) k_seg_sort_medium(const int32_t *__restrict__ cand_offsets, int32_t *ids,
+                                                         long long capacity, const ProbeHeader *h,
+                                                         const int *medium_list)
+{
+    __shared__ int s_v[8 * SORT_WARP_SMEM];
+    const int lane = threadIdx.x & 31;
+    int *wv = s_v + (threadIdx.x >> 5) * SORT_WARP_SMEM;
+    const int nm = h->n_medium;
+    const long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+    for (long long t = gw; t < nm; t += nw) {
+        const int k = medium_list[t];
+        const long long a = min((long long)cand_offsets[k], capacity);
+        const long long n = min((long long)cand_offsets[k + 1], capacity) - a;
+        if (n <= 32) {
+            int v = lane < n ? ids[a + lane] : INT_MAX;
+            v = warp_sort32(v, lane);
+            if (lane < n) ids[a + lane] = v;
+        } else {
+            for (int i = lane; i < n; i += 32) wv[i] = ids[a + i];
+            __syncwarp();
+            bitonic_sort(wv, (int)n, lane, 32, [] { __syncwarp(); });
+            for (int i = lane; i < n; i += 32) ids[a + i] = wv[i];
+            __syncwarp();
         }
     }
 }
@@ -549,7 +632,7 @@ __global__ void __launch_bounds__(256) k_seg_sort(const int32_t *__restrict__ ca
 // The queued longer lists, one CTA per polygon: in shared memory up to SORT_CTA_SMEM ids, else in
 // place in global memory.
 __global__ void __launch_bounds__(256) k_seg_sort_long(const int32_t *__restrict__ cand_offsets, int32_t *ids,
-                                                       long long capacity, const BinHeader *h,
+                                                       long long capacity, const ProbeHeader *h,
                                                        const int *long_list)
 {
     __shared__ int s_v[SORT_CTA_SMEM];
@@ -571,7 +654,7 @@ __global__ void __launch_bounds__(256) k_seg_sort_long(const int32_t *__restrict
     }
 }
 
-__global__ void k_bin_finish(BinHeader *h, const long long *d_total, long long capacity, int32_t *d_overflow)
+__global__ void k_bin_finish(ProbeHeader *h, const long long *d_total, long long capacity, int32_t *d_overflow)
 {
     if (threadIdx.x == 0 && blockIdx.x == 0) {
         if (d_total) h->total = *d_total;
@@ -582,14 +665,13 @@ __global__ void k_bin_finish(BinHeader *h, const long long *d_total, long long c
 // ------------------------------------------------------------------------------------------
 // host launch sequences
 // ------------------------------------------------------------------------------------------
-int launch_bin_count(const int2 *points, long long N, const int32_t *po, const int2 *verts, int P, int cell_size,
-                     void *ws, size_t ws_bytes, int32_t *cand_offsets, long long *d_total, int n_sm,
-                     cudaStream_t s)
+int launch_bin_index(const int32_t *po, const int2 *verts, int P, int cell_size, void *index, size_t index_bytes,
+                     int n_sm, cudaStream_t s)
 {
-    const BinLayout L = bin_layout(N, P);
-    if (ws_bytes < L.total) return (int)cudaErrorInvalidValue;
-    char *w = static_cast<char *>(ws);
-    BinHeader *h = reinterpret_cast<BinHeader *>(w + L.header);
+    const IndexLayout L = index_layout(P);
+    if (index_bytes < L.total) return (int)cudaErrorInvalidValue;
+    char *w = static_cast<char *>(index);
+    IndexHeader *h = reinterpret_cast<IndexHeader *>(w + L.header);
     int4 *bb = reinterpret_cast<int4 *>(w + L.poly_bb);
     CellEntry *ent = reinterpret_cast<CellEntry *>(w + L.ent);
     unsigned *cnt = reinterpret_cast<unsigned *>(w + L.cnt);
@@ -605,10 +687,8 @@ int launch_bin_count(const int2 *points, long long N, const int32_t *po, const i
         while (requested < 31 && (1LL << requested) < cell_size) ++requested;
     }
     int e;
-
-    k_bin_init<<<1, 32, 0, s>>>(h, requested, d_total);
+    k_index_init<<<1, 32, 0, s>>>(h, requested, P);
     note_launch();
-    if ((e = (int)cudaMemsetAsync(cand_offsets, 0, ((size_t)P + 1) * 4, s))) return e;
     if (P > 0) {
         k_poly_bbox<<<grid, 256, 0, s>>>(po, verts, P, bb, h);
         k_bin_level<<<1, 32, 0, s>>>(h, L.lcap);
@@ -622,17 +702,89 @@ int launch_bin_count(const int2 *points, long long N, const int32_t *po, const i
         k_cells<false><<<grid, 256, 0, s>>>(bb, po, P, h, ent, cnt, off, list_bb, list_id, big, L.hbits);
         k_cells_pack<<<grid, 256, 0, s>>>(cnt, off, ent, L.H);
         note_launch(2);
-        if (N > 0) {
-            k_probe_count<<<grid, PROBE_THREADS, 0, s>>>(points, N, h, ent, list_bb, list_id, big, bb, L.hbits,
-                                                         reinterpret_cast<unsigned *>(cand_offsets),
-                                                         reinterpret_cast<int2 *>(w + L.pairs), L.pcap, d_total);
-            note_launch();
-        }
-        if ((e = scan_exclusive(reinterpret_cast<unsigned *>(cand_offsets), (long long)P + 1, tmp, s))) return e;
     }
-    k_bin_finish<<<1, 32, 0, s>>>(h, d_total, 0, nullptr);
+    k_index_finish<<<1, 32, 0, s>>>(h);
     note_launch();
     return (int)cudaGetLastError();
+}
+
+int launch_bin_probe_count(const int2 *points, long long N, const void *index, size_t index_bytes, int P,
+                           void *probe, size_t probe_bytes, int32_t *cand_offsets, long long *d_total, int n_sm,
+                           cudaStream_t s)
+{
+    const IndexLayout L = index_layout(P);
+    const ProbeLayout Q = probe_layout(N, P);
+    if (index_bytes < L.total || probe_bytes < Q.total) return (int)cudaErrorInvalidValue;
+    const char *w = static_cast<const char *>(index);
+    char *pw = static_cast<char *>(probe);
+    const IndexHeader *h = reinterpret_cast<const IndexHeader *>(w + L.header);
+    ProbeHeader *q = reinterpret_cast<ProbeHeader *>(pw + Q.header);
+    int e;
+    k_probe_init<<<1, 32, 0, s>>>(q, d_total);
+    note_launch();
+    if ((e = (int)cudaMemsetAsync(cand_offsets, 0, ((size_t)P + 1) * 4, s))) return e;
+    if (P > 0) {
+        if (N > 0) {
+            k_probe_count<<<n_sm * 8, PROBE_THREADS, 0, s>>>(
+                points, N, h, P, q, reinterpret_cast<const CellEntry *>(w + L.ent),
+                reinterpret_cast<const int4 *>(w + L.list_bb), reinterpret_cast<const int *>(w + L.list_id),
+                reinterpret_cast<const int *>(w + L.big), reinterpret_cast<const int4 *>(w + L.poly_bb), L.hbits,
+                reinterpret_cast<unsigned *>(cand_offsets), reinterpret_cast<int2 *>(pw + Q.pairs), Q.pcap, d_total);
+            note_launch();
+        }
+        if ((e = scan_exclusive(reinterpret_cast<unsigned *>(cand_offsets), (long long)P + 1,
+                                reinterpret_cast<unsigned *>(pw + Q.scan_tmp), s)))
+            return e;
+    }
+    k_bin_finish<<<1, 32, 0, s>>>(q, d_total, 0, nullptr);
+    note_launch();
+    return (int)cudaGetLastError();
+}
+
+int launch_bin_probe_fill(const int2 *points, long long N, const void *index, size_t index_bytes, int P,
+                          void *probe, size_t probe_bytes, const int32_t *cand_offsets, int32_t *cand_ids,
+                          long long capacity, int32_t *d_overflow, int n_sm, cudaStream_t s)
+{
+    const IndexLayout L = index_layout(P);
+    const ProbeLayout Q = probe_layout(N, P);
+    if (index_bytes < L.total || probe_bytes < Q.total) return (int)cudaErrorInvalidValue;
+    const char *w = static_cast<const char *>(index);
+    char *pw = static_cast<char *>(probe);
+    const IndexHeader *h = reinterpret_cast<const IndexHeader *>(w + L.header);
+    ProbeHeader *q = reinterpret_cast<ProbeHeader *>(pw + Q.header);
+    unsigned *cursor = reinterpret_cast<unsigned *>(pw + Q.cursor);
+    int *medium_list = reinterpret_cast<int *>(pw + Q.medium_list);
+    int *long_list = reinterpret_cast<int *>(pw + Q.long_list);
+    const int grid = n_sm * 8;
+    int e;
+    if (P > 0 && N > 0) {
+        if ((e = (int)cudaMemsetAsync(cursor, 0, (size_t)P * 4, s))) return e;
+        if ((e = (int)cudaMemsetAsync(&q->n_long, 0, 2 * sizeof(int), s))) return e;   // n_long, n_medium
+        k_probe_fill<<<grid, PROBE_THREADS, 0, s>>>(
+            points, N, h, P, q, reinterpret_cast<const CellEntry *>(w + L.ent),
+            reinterpret_cast<const int4 *>(w + L.list_bb), reinterpret_cast<const int *>(w + L.list_id),
+            reinterpret_cast<const int *>(w + L.big), reinterpret_cast<const int4 *>(w + L.poly_bb), L.hbits,
+            reinterpret_cast<const int2 *>(pw + Q.pairs), Q.pcap, cand_offsets, cursor, cand_ids, capacity);
+        k_seg_sort<<<grid, 256, 0, s>>>(cand_offsets, P, cand_ids, capacity, q, medium_list, long_list);
+        k_seg_sort_medium<<<grid, 256, 0, s>>>(cand_offsets, cand_ids, capacity, q, medium_list);
+        k_seg_sort_long<<<n_sm * 4, 256, 0, s>>>(cand_offsets, cand_ids, capacity, q, long_list);
+        note_launch(4);
+    }
+    k_bin_finish<<<1, 32, 0, s>>>(q, nullptr, capacity, d_overflow);
+    note_launch();
+    return (int)cudaGetLastError();
+}
+
+int launch_bin_count(const int2 *points, long long N, const int32_t *po, const int2 *verts, int P, int cell_size,
+                     void *ws, size_t ws_bytes, int32_t *cand_offsets, long long *d_total, int n_sm,
+                     cudaStream_t s)
+{
+    const size_t ib = bin_index_bytes(P), pb = bin_probe_bytes(N, P);
+    if (ws_bytes < ib + pb) return (int)cudaErrorInvalidValue;
+    int e = launch_bin_index(po, verts, P, cell_size, ws, ib, n_sm, s);
+    if (e) return e;
+    return launch_bin_probe_count(points, N, ws, ib, P, static_cast<char *>(ws) + ib, pb, cand_offsets, d_total,
+                                  n_sm, s);
 }
 
 int launch_bin_fill(const int2 *points, long long N, const int32_t *po, const int2 *verts, int P, void *ws,
@@ -641,32 +793,10 @@ int launch_bin_fill(const int2 *points, long long N, const int32_t *po, const in
 {
     (void)verts;
     (void)po;
-    const BinLayout L = bin_layout(N, P);
-    if (ws_bytes < L.total) return (int)cudaErrorInvalidValue;
-    char *w = static_cast<char *>(ws);
-    BinHeader *h = reinterpret_cast<BinHeader *>(w + L.header);
-    const int4 *bb = reinterpret_cast<const int4 *>(w + L.poly_bb);
-    const CellEntry *ent = reinterpret_cast<const CellEntry *>(w + L.ent);
-    const int4 *list_bb = reinterpret_cast<const int4 *>(w + L.list_bb);
-    const int *list_id = reinterpret_cast<const int *>(w + L.list_id);
-    const int *big = reinterpret_cast<const int *>(w + L.big);
-    unsigned *cursor = reinterpret_cast<unsigned *>(w + L.cursor);
-    int *long_list = reinterpret_cast<int *>(w + L.long_list);
-    const int grid = n_sm * 8;
-    int e;
-    if (P > 0 && N > 0) {
-        if ((e = (int)cudaMemsetAsync(cursor, 0, (size_t)P * 4, s))) return e;
-        if ((e = (int)cudaMemsetAsync(&h->n_long, 0, sizeof(int), s))) return e;
-        k_probe_fill<<<grid, PROBE_THREADS, 0, s>>>(points, N, h, ent, list_bb, list_id, big, bb, L.hbits,
-                                                    reinterpret_cast<const int2 *>(w + L.pairs), L.pcap,
-                                                    cand_offsets, cursor, cand_ids, capacity);
-        k_seg_sort<<<grid, 256, 0, s>>>(cand_offsets, P, cand_ids, capacity, h, long_list);
-        k_seg_sort_long<<<n_sm * 4, 256, 0, s>>>(cand_offsets, cand_ids, capacity, h, long_list);
-        note_launch(3);
-    }
-    k_bin_finish<<<1, 32, 0, s>>>(h, nullptr, capacity, d_overflow);
-    note_launch();
-    return (int)cudaGetLastError();
+    const size_t ib = bin_index_bytes(P), pb = bin_probe_bytes(N, P);
+    if (ws_bytes < ib + pb) return (int)cudaErrorInvalidValue;
+    return launch_bin_probe_fill(points, N, ws, ib, P, static_cast<char *>(ws) + ib, pb, cand_offsets, cand_ids,
+                                 capacity, d_overflow, n_sm, s);
 }
 
 }  // namespace pipdev

@@ -394,6 +394,80 @@ int pip_bin_fill(const int32_t *points, int64_t n_points, const int32_t *poly_of
     return e == 0 ? PIP_OK : cuda_fail((cudaError_t)e);
 }
 
+size_t pip_bin_index_bytes(int32_t n_polys)
+{
+    if (n_polys < 0) return 0;
+    return bin_index_bytes(n_polys);
+}
+
+size_t pip_bin_probe_bytes(int64_t n_points, int32_t n_polys)
+{
+    if (n_points < 0 || n_polys < 0) return 0;
+    return bin_probe_bytes(n_points, n_polys);
+}
+
+int pip_bin_index(const int32_t *poly_offsets, const int32_t *verts, int32_t n_polys, int32_t cell_size,
+                  void *index, size_t index_bytes, void *stream)
+{
+    if (n_polys < 0 || cell_size < 0) return PIP_ERR_SIZE;
+    if (!index) return PIP_ERR_NULL;
+    if (n_polys > 0 && (!poly_offsets || !verts)) return PIP_ERR_NULL;
+    if (misaligned(verts, 8) || misaligned(index, 16) || misaligned(poly_offsets, 4)) return PIP_ERR_ALIGN;
+    if (index_bytes < bin_index_bytes(n_polys)) return PIP_ERR_WORKSPACE;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    DeviceState *ds = nullptr;
+    int rc = device_state(s, &ds);
+    if (rc != PIP_OK) return rc;
+    int e = launch_bin_index(poly_offsets, reinterpret_cast<const int2 *>(verts), n_polys, cell_size, index,
+                             index_bytes, ds->n_sm, s);
+    return e == 0 ? PIP_OK : cuda_fail((cudaError_t)e);
+}
+
+int pip_bin_probe_count(const int32_t *points, int64_t n_points, const void *index, size_t index_bytes,
+                        int32_t n_polys, void *probe, size_t probe_bytes, int32_t *cand_offsets,
+                        int64_t *d_total, void *stream)
+{
+    if (n_points < 0 || n_polys < 0) return PIP_ERR_SIZE;
+    if (n_points > (int64_t)INT_MAX) return PIP_ERR_TOO_LARGE;
+    if (!index || !probe || !cand_offsets || !d_total) return PIP_ERR_NULL;
+    if (n_points > 0 && !points) return PIP_ERR_NULL;
+    if (misaligned(points, 8) || misaligned(index, 16) || misaligned(probe, 16) || misaligned(d_total, 8) ||
+        misaligned(cand_offsets, 4))
+        return PIP_ERR_ALIGN;
+    if (index_bytes < bin_index_bytes(n_polys) || probe_bytes < bin_probe_bytes(n_points, n_polys))
+        return PIP_ERR_WORKSPACE;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    DeviceState *ds = nullptr;
+    int rc = device_state(s, &ds);
+    if (rc != PIP_OK) return rc;
+    int e = launch_bin_probe_count(reinterpret_cast<const int2 *>(points), n_points, index, index_bytes, n_polys,
+                                   probe, probe_bytes, cand_offsets, reinterpret_cast<long long *>(d_total),
+                                   ds->n_sm, s);
+    return e == 0 ? PIP_OK : cuda_fail((cudaError_t)e);
+}
+
+int pip_bin_probe_fill(const int32_t *points, int64_t n_points, const void *index, size_t index_bytes,
+                       int32_t n_polys, void *probe, size_t probe_bytes, const int32_t *cand_offsets,
+                       int32_t *cand_ids, int64_t capacity, int32_t *d_overflow, void *stream)
+{
+    if (n_points < 0 || n_polys < 0 || capacity < 0) return PIP_ERR_SIZE;
+    if (n_points > (int64_t)INT_MAX) return PIP_ERR_TOO_LARGE;
+    if (!index || !probe || !cand_offsets || (capacity > 0 && !cand_ids)) return PIP_ERR_NULL;
+    if (n_points > 0 && !points) return PIP_ERR_NULL;
+    if (misaligned(points, 8) || misaligned(index, 16) || misaligned(probe, 16) || misaligned(cand_ids, 4) ||
+        misaligned(cand_offsets, 4) || misaligned(d_overflow, 4))
+        return PIP_ERR_ALIGN;
+    if (index_bytes < bin_index_bytes(n_polys) || probe_bytes < bin_probe_bytes(n_points, n_polys))
+        return PIP_ERR_WORKSPACE;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    DeviceState *ds = nullptr;
+    int rc = device_state(s, &ds);
+    if (rc != PIP_OK) return rc;
+    int e = launch_bin_probe_fill(reinterpret_cast<const int2 *>(points), n_points, index, index_bytes, n_polys,
+                                  probe, probe_bytes, cand_offsets, cand_ids, capacity, d_overflow, ds->n_sm, s);
+    return e == 0 ? PIP_OK : cuda_fail((cudaError_t)e);
+}
+
 const char *pip_status_str(int code)
 {
     switch (code) {

@@ -95,7 +95,10 @@ __global__ void __launch_bounds__(256) k_pip_exact(ClassifyArgs a, long long tot
                 k = l2;
             }
             if (c >= C) k = -1;
-            if (k >= 0) pid = __ldg(a.cand_ids + c);
+            if (k >= 0) {
+                pid = __ldg(a.cand_ids + c);
+                if (pid < 0 || pid >= a.n_points) k = -1;   // an id outside the points: no candidate
+            }
         }
         int inside = 0;
         if (k >= 0) {

@@ -840,7 +840,7 @@ __global__ void __launch_bounds__(LG_THREADS, PPT == 4 ? 3 : 4) k_pip_large(Clas
             pt[r] = make_int2(0, 0);
             if (ok[r]) {
                 long long pid = dense ? c - (long long)k * W32 : (long long)__ldg(a.cand_ids + c);
-                if (pid >= a.n_points) ok[r] = false;
+                if (pid < 0 || pid >= a.n_points) ok[r] = false;   // an id outside the points: no candidate
                 else pt[r] = __ldg(a.points + pid);
             }
             if (ok[r]) {

@@ -46,6 +46,17 @@ int launch_quantize(const double *v, long long n, double scale, int32_t *out, in
 
 // binning
 size_t bin_workspace_bytes(long long n_points, int n_polys);
+size_t bin_index_bytes(int n_polys);
+size_t bin_probe_bytes(long long n_points, int n_polys);
+int launch_bin_index(const int32_t *poly_offsets, const int2 *verts, int n_polys, int cell_size, void *index,
+                     size_t index_bytes, int n_sm, cudaStream_t stream);
+int launch_bin_probe_count(const int2 *points, long long n_points, const void *index, size_t index_bytes,
+                           int n_polys, void *probe, size_t probe_bytes, int32_t *cand_offsets,
+                           long long *d_total, int n_sm, cudaStream_t stream);
+int launch_bin_probe_fill(const int2 *points, long long n_points, const void *index, size_t index_bytes,
+                          int n_polys, void *probe, size_t probe_bytes, const int32_t *cand_offsets,
+                          int32_t *cand_ids, long long capacity, int32_t *d_overflow, int n_sm,
+                          cudaStream_t stream);
 int launch_bin_count(const int2 *points, long long n_points, const int32_t *poly_offsets,
                      const int2 *verts, int n_polys, int cell_size, void *ws, size_t ws_bytes,
                      int32_t *cand_offsets, long long *d_total, int n_sm, cudaStream_t stream);

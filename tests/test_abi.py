@@ -104,7 +104,32 @@ def test_bin_workspace_size_grows(lib):
     c = lib.pip_bin_workspace_bytes(0, 100_000)
     assert 0 < a < b and 0 < c < b
     assert c >= 100_000 * (16 + 2 * 8 + 4)
-    assert b - c >= 10_000_000 // 4 * 8
+    assert b - c >= 10_000_000 // 2 * 8
+    # one-step workspace = index + one probe workspace
+    assert b == lib.pip_bin_index_bytes(100_000) + lib.pip_bin_probe_bytes(10_000_000, 100_000)
+    assert lib.pip_bin_index_bytes(-1) == 0 and lib.pip_bin_probe_bytes(-1, 10) == 0
+
+
+def test_argument_checks_of_the_binning_index(lib):
+    from paper_2306_04316_gb300 import _lib
+    P = ctypes.c_void_p
+    a8, a16 = P(0x1000), P(0x10000)
+    ib, pb = lib.pip_bin_index_bytes(10), lib.pip_bin_probe_bytes(100, 10)
+    assert lib.pip_bin_index(a8, a8, -1, 0, a16, ib, None) == _lib.PIP_ERR_SIZE
+    assert lib.pip_bin_index(a8, a8, 10, -1, a16, ib, None) == _lib.PIP_ERR_SIZE
+    assert lib.pip_bin_index(None, a8, 10, 0, a16, ib, None) == _lib.PIP_ERR_NULL
+    assert lib.pip_bin_index(a8, a8, 10, 0, None, ib, None) == _lib.PIP_ERR_NULL
+    assert lib.pip_bin_index(a8, a8, 10, 0, P(0x10008), ib, None) == _lib.PIP_ERR_ALIGN
+    assert lib.pip_bin_index(a8, a8, 10, 0, a16, ib - 1, None) == _lib.PIP_ERR_WORKSPACE
+    assert lib.pip_bin_probe_count(a8, -1, a16, ib, 10, a16, pb, a8, a8, None) == _lib.PIP_ERR_SIZE
+    assert lib.pip_bin_probe_count(a8, 100, None, ib, 10, a16, pb, a8, a8, None) == _lib.PIP_ERR_NULL
+    assert lib.pip_bin_probe_count(a8, 100, a16, ib, 10, a16, pb, a8, None, None) == _lib.PIP_ERR_NULL
+    assert lib.pip_bin_probe_count(a8, 100, a16, ib, 10, P(0x10004), pb, a8, a8, None) == _lib.PIP_ERR_ALIGN
+    assert lib.pip_bin_probe_count(a8, 100, a16, ib - 1, 10, a16, pb, a8, a8, None) == _lib.PIP_ERR_WORKSPACE
+    assert lib.pip_bin_probe_count(a8, 100, a16, ib, 10, a16, pb - 1, a8, a8, None) == _lib.PIP_ERR_WORKSPACE
+    assert lib.pip_bin_probe_fill(a8, 100, a16, ib, 10, a16, pb, a8, a8, -1, None, None) == _lib.PIP_ERR_SIZE
+    assert lib.pip_bin_probe_fill(a8, 100, a16, ib, 10, a16, pb, a8, None, 5, None, None) == _lib.PIP_ERR_NULL
+    assert lib.pip_bin_probe_fill(a8, 100, a16, ib, 10, a16, pb - 1, a8, a8, 5, None, None) == _lib.PIP_ERR_WORKSPACE
 
 
 def test_argument_checks_of_the_other_entry_points(lib):

@@ -244,6 +244,30 @@ def test_binning_is_deterministic(api):
     assert torch.equal(co1, co2) and torch.equal(ids1, ids2)
 
 
+@pytest.mark.parametrize("exact", [False, True])
+def test_out_of_range_ids_read_nothing(api, exact):
+    """Candidate ids outside [0, n_points) are never dereferenced: their bits are 0 and every
+    valid candidate keeps its oracle bit, for small polygons and for a large one."""
+    rng = np.random.default_rng(5)
+    small = make("small", [[(0, 0), (100, 0), (100, 100), (0, 100)]] * 3, rng.integers(-10, 110, (500, 2)),
+                 csr=[range(500)] * 3)
+    big = make("big", [_star_polygon(rng, 600, 50_000)], rng.integers(-60_000, 60_000, (3000, 2)),
+               csr=[range(3000)])
+    w = _concat([small, big], "mixed")
+    ids = w.cand_ids.copy()
+    bad = rng.choice(len(ids), 200, replace=False)
+    ids[bad[:100]] = -1 - rng.integers(0, 2**31 - 1, 100)
+    ids[bad[100:]] = w.n_points + rng.integers(0, 2**31 - 1 - w.n_points, 100)
+    got = oracle.unpack_bits(gpu_bits(api, w.with_csr(w.cand_offsets, ids.astype(np.int32)), exact=exact),
+                             w.n_bits)
+    want = oracle.unpack_bits(oracle.classify(w.points, w.poly_offsets, w.verts, w.cand_offsets, w.cand_ids),
+                              w.n_bits)
+    keep = np.ones(w.n_bits, bool)
+    keep[bad] = False
+    assert not got[bad].any()
+    assert np.array_equal(got[keep], want[keep])
+
+
 def _bin_case(rng):
     """Polygons that exercise every path of the binning: tiny boxes, boxes large enough to go on
     the short list, empty polygons, and id lists long enough for each sort (warp registers,
@@ -287,6 +311,45 @@ def test_binning_paths_and_cell_sizes(api, cell_size):
     assert ((counts > 32) & (counts <= 1024)).any()
     assert np.array_equal(np.diff(co.cpu().numpy().astype(np.int64)), counts)
     assert np.array_equal(ids.cpu().numpy(), want_ids)
+
+
+def test_binning_index_probed_by_several_batches(api):
+    """One polygon index, three batches of points probed on two streams at once (each with its
+    own probe workspace): every batch's CSR equals the oracle's; an index built for another
+    polygon count, or never built, yields no candidates."""
+    rng = np.random.default_rng(78)
+    pts0, po, verts = _bin_case(rng)
+    P = len(po) - 1
+    d_po, d_v = torch.from_numpy(po).cuda(), torch.from_numpy(verts).cuda()
+    index = api.bin_index(d_po, d_v)
+    batches = [pts0, rng.permutation(pts0)[:200_000], rng.integers(-10**6, 10**6, (50_000, 2)).astype(np.int32)]
+    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    torch.cuda.synchronize()
+    out = []
+    for b, pts in enumerate(batches):
+        st = streams[b % 2]
+        d_pts = torch.from_numpy(pts).cuda()
+        torch.cuda.synchronize()
+        with torch.cuda.stream(st):
+            co, tot, probe = api.pip_bin_probe_count(d_pts, index, P, stream=st)
+            st.synchronize()
+            ids = torch.empty(max(int(tot.item()), 1), dtype=torch.int32, device="cuda")
+            ovf = torch.zeros(1, dtype=torch.int32, device="cuda")
+            api.pip_bin_probe_fill(d_pts, index, P, probe, co, ids, d_overflow=ovf, stream=st)
+        out.append((co, tot, ids, ovf, pts))
+    torch.cuda.synchronize()
+    for co, tot, ids, ovf, pts in out:
+        counts, want_ids = oracle.bbox_join(pts, po, verts, np.arange(P))
+        assert int(ovf.item()) == 0 and int(tot.item()) == counts.sum()
+        assert np.array_equal(np.diff(co.cpu().numpy().astype(np.int64)), counts)
+        assert np.array_equal(ids[:int(tot.item())].cpu().numpy(), want_ids)
+    d_pts = torch.from_numpy(pts0).cuda()
+    co, tot, _ = api.pip_bin_probe_count(d_pts, index, P - 1)             # another polygon count
+    fresh = torch.zeros_like(index)                                        # never built
+    co2, tot2, _ = api.pip_bin_probe_count(d_pts, fresh, P)
+    torch.cuda.synchronize()
+    assert int(tot.item()) == 0 and not co.any()
+    assert int(tot2.item()) == 0 and not co2.any()
 
 
 def _concat(ws, name):
