@@ -112,6 +112,21 @@ __device__ __noinline__ int exact_parity(const int2 *v, int e0, int e1, bool wra
     return parity;
 }
 
+// Exact parity of the point (px, py) over the same edges, computed by the 32 lanes of a warp
+// together (lane l takes edges e0 + l, e0 + l + 32, ...); every lane returns it.  All lanes must
+// call it.  The rare recheck of one lane's candidate then costs its warp about (e1 - e0) / 32
+// exact tests instead of e1 - e0.
+__device__ __forceinline__ int warp_exact_parity(const int2 *v, int e0, int e1, bool wrap, int px, int py, int lane)
+{
+    int part = 0;
+    for (int e = e0 + lane; e < e1; e += 32) {
+        const int nx = (wrap && e + 1 == e1) ? e0 : e + 1;
+        const int2 ri = v[e], rj = v[nx];
+        if ((ri.y > py) != (rj.y > py)) part ^= exact_edge_counts(px, py, ri.x, ri.y, rj.x, rj.y);
+    }
+    return __popc(__ballot_sync(FULL, part)) & 1;
+}
+
 // =============================================================================================
 // k_pip_warp -- small polygons; every warp works on its own runs of consecutive polygons
 // =============================================================================================
@@ -532,13 +547,17 @@ __global__ void __launch_bounds__(WP_THREADS, WP_CTAS) k_pip_warp(ClassifyArgs a
                                 par ^= (int)(st & (tt > 0.f));
                                 unc |= st & (fabsf(tt) <= B);
                             }
-                            if (gf) {
-                                parity = par;
-                                if (unc) {
-                                    ++st_fbp;
-                                    parity = exact_parity(S.v, e0, e1, true, p2);
-                                }
+                            if (gf) parity = par;
+                            // candidates whose FP32 sign came within the bound of zero: their
+                            // polygon's exact parity, each by the whole warp
+                            for (unsigned um = __ballot_sync(FULL, gf && unc); um; um &= um - 1) {
+                                const int src = __ffs(um) - 1;
+                                const int q = warp_exact_parity(S.v, __shfl_sync(FULL, e0, src), __shfl_sync(FULL, e1, src),
+                                                                true, __shfl_sync(FULL, p2.x, src),
+                                                                __shfl_sync(FULL, p2.y, src), lane);
+                                if (lane == src) parity = q;
                             }
+                            if (gf && unc) ++st_fbp;
                         }
                     }
                     const unsigned bits = __ballot_sync(FULL, parity);
@@ -678,15 +697,21 @@ __device__ __forceinline__ void tile_parity_scaled(const int4 *__restrict__ s_re
             unc[r] |= x & __float_as_uint(d);
         }
     }
+    // candidates whose FP32 sign came within the bound of zero: the tile's exact parity, each by
+    // the whole warp (every thread of the CTA is here)
+    const int lane = threadIdx.x & 31;
     #pragma unroll
     for (int r = 0; r < PPT; ++r) {
-        if (!ok[r]) continue;
+        const bool u = ok[r] && (unc[r] >> 31);
         int pr = (int)(acc[r] >> 31);
-        if (unc[r] >> 31) {
-            ++n_fb_pts;
-            pr = exact_parity(s_v, 0, nt, false, p[r]);
+        for (unsigned um = __ballot_sync(FULL, u); um; um &= um - 1) {
+            const int src = __ffs(um) - 1;
+            const int q = warp_exact_parity(s_v, 0, nt, false, __shfl_sync(FULL, p[r].x, src),
+                                            __shfl_sync(FULL, p[r].y, src), lane);
+            if (lane == src) pr = q;
         }
-        par[r] ^= pr;
+        if (u) ++n_fb_pts;
+        if (ok[r]) par[r] ^= pr;
     }
 }
 
