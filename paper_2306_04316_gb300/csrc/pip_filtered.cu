@@ -114,8 +114,10 @@ __device__ __noinline__ int exact_parity(const int2 *v, int e0, int e1, bool wra
 
 // Exact parity of the point (px, py) over the same edges, computed by the 32 lanes of a warp
 // together (lane l takes edges e0 + l, e0 + l + 32, ...); every lane returns it.  All lanes must
-// call it.  The rare recheck of one lane's candidate then costs its warp about (e1 - e0) / 32
-// exact tests instead of e1 - e0.
+// call it.  The rare recheck of one lane's candidate over a large polygon's tile then costs its
+// warp about (e1 - e0) / 32 exact tests instead of e1 - e0.  (The small-polygon kernel keeps the
+// per-lane exact_parity: its polygons have at most 256 edges, and the warp-wide form there
+// measured more instructions on the footprint batch, whose polygons never take this path.)
 __device__ __forceinline__ int warp_exact_parity(const int2 *v, int e0, int e1, bool wrap, int px, int py, int lane)
 {
     int part = 0;
@@ -286,11 +288,13 @@ __global__ void __launch_bounds__(WP_THREADS, WP_CTAS) k_pip_warp(ClassifyArgs a
                 atomicExch(&ll->overflow, 1);
             }
         }
-        // large polygons' bits are 0 here; k_pip_large XORs their parities in afterwards
-        for (unsigned m = lgm; m; m &= m - 1) {
-            const int l = __ffs(m) - 1;
-            zero_bits(a.out_bits, (long long)__shfl_sync(FULL, cb, l), (long long)__shfl_sync(FULL, ce, l), lane);
-        }
+        // large polygons' bits are 0 here; k_pip_large XORs their parities in afterwards (a dense
+        // output is zeroed before this kernel)
+        if (!DENSE)
+            for (unsigned m = lgm; m; m &= m - 1) {
+                const int l = __ffs(m) - 1;
+                zero_bits(a.out_bits, (long long)__shfl_sync(FULL, cb, l), (long long)__shfl_sync(FULL, ce, l), lane);
+            }
 
         int p = 0;
         while (p < np) {
@@ -547,17 +551,13 @@ __global__ void __launch_bounds__(WP_THREADS, WP_CTAS) k_pip_warp(ClassifyArgs a
                                 par ^= (int)(st & (tt > 0.f));
                                 unc |= st & (fabsf(tt) <= B);
                             }
-                            if (gf) parity = par;
-                            // candidates whose FP32 sign came within the bound of zero: their
-                            // polygon's exact parity, each by the whole warp
-                            for (unsigned um = __ballot_sync(FULL, gf && unc); um; um &= um - 1) {
-                                const int src = __ffs(um) - 1;
-                                const int q = warp_exact_parity(S.v, __shfl_sync(FULL, e0, src), __shfl_sync(FULL, e1, src),
-                                                                true, __shfl_sync(FULL, p2.x, src),
-                                                                __shfl_sync(FULL, p2.y, src), lane);
-                                if (lane == src) parity = q;
+                            if (gf) {
+                                parity = par;
+                                if (unc) {
+                                    ++st_fbp;
+                                    parity = exact_parity(S.v, e0, e1, true, p2);
+                                }
                             }
-                            if (gf && unc) ++st_fbp;
                         }
                     }
                     const unsigned bits = __ballot_sync(FULL, parity);
@@ -1070,6 +1070,12 @@ template <bool VERIFY>
 static int launch_filtered_v(const ClassifyArgs &a, long long total_bits, const Tuning &t, int n_sm, LargeList *ll,
                              int lcap, cudaStream_t stream)
 {
+    if (!a.cand_offsets && a.n_polys > 0 && a.words_per_poly > 0) {
+        // dense output zeroed up front (one memset node), so that no warp of k_pip_warp has to
+        // clear a large polygon's words on its own
+        const cudaError_t m = cudaMemsetAsync(a.out_bits, 0, (size_t)a.n_polys * (size_t)a.words_per_poly * 4, stream);
+        if (m != cudaSuccess) return (int)m;
+    }
     int e = a.cand_offsets ? launch_warp_d<false, VERIFY>(a, ll, lcap, n_sm, stream)
                            : launch_warp_d<true, VERIFY>(a, ll, lcap, n_sm, stream);
     if (e) return e;
