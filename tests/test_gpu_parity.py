@@ -313,6 +313,43 @@ def test_binning_paths_and_cell_sizes(api, cell_size):
     assert np.array_equal(ids.cpu().numpy(), want_ids)
 
 
+def test_binning_degenerate_inputs(api):
+    """Empty point sets and polygon sets, boxes of zero width or height, points exactly on box
+    edges and corners (closed boxes include them), and more (polygon, point) pairs than the
+    probe workspace records (the fill pass then probes the points again): every list equals
+    the oracle's."""
+    rng = np.random.default_rng(79)
+    polys = [np.array([[0, 0], [0, 1000], [0, 500]], dtype=np.int64),          # zero width
+             np.array([[0, 0], [1000, 0], [500, 0]], dtype=np.int64),          # zero height
+             np.array([[5, 5]], dtype=np.int64),                                # a single vertex
+             np.array([[-100, -100], [100, -100], [100, 100], [-100, 100]], dtype=np.int64)]
+    polys += [np.array([[-50 - i, -50], [50, -50 - i], [50 + i, 50], [-50, 50 + i]], dtype=np.int64)
+              for i in range(600)]                                             # 600 overlapping boxes
+    po = np.zeros(len(polys) + 1, dtype=np.int64)
+    po[1:] = np.cumsum([len(q) for q in polys])
+    verts = np.concatenate(polys).astype(np.int32)
+    edge_pts = [(0, 0), (0, 1000), (0, 500), (1000, 0), (500, 0), (5, 5), (-100, -100), (100, 100),
+                (-100, 100), (100, -100), (0, 1001), (1001, 0), (-101, 0)]
+    pts = np.concatenate([np.array(edge_pts), rng.integers(-120, 120, (2000, 2))]).astype(np.int32)
+    P = len(po) - 1
+    d_po, d_v = torch.from_numpy(po.astype(np.int32)).cuda(), torch.from_numpy(verts).cuda()
+    for case_pts in (pts, pts[:0]):
+        d_pts = torch.from_numpy(np.ascontiguousarray(case_pts)).cuda()
+        co, ids = api.bin_join(d_pts, d_po, d_v)
+        torch.cuda.synchronize()
+        counts, want_ids = oracle.bbox_join(case_pts, po.astype(np.int32), verts, np.arange(P))
+        if len(case_pts):
+            assert counts.sum() > len(case_pts) // 2 + 1024        # past what the probe records
+        assert np.array_equal(np.diff(co.cpu().numpy().astype(np.int64)), counts)
+        assert np.array_equal(ids.cpu().numpy(), want_ids)
+    # no polygons at all
+    e_po = torch.zeros(1, dtype=torch.int32, device="cuda")
+    e_v = torch.zeros((0, 2), dtype=torch.int32, device="cuda")
+    co, ids = api.bin_join(torch.from_numpy(pts).cuda(), e_po, e_v)
+    torch.cuda.synchronize()
+    assert co.cpu().tolist() == [0] and ids.numel() == 0
+
+
 def test_binning_index_probed_by_several_batches(api):
     """One polygon index, three batches of points probed on two streams at once (each with its
     own probe workspace): every batch's CSR equals the oracle's; an index built for another
