@@ -446,6 +446,8 @@ def main():
     ap.add_argument("--scale", type=float, default=1.0, help="fraction of the full batch (tests only)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-graph", action="store_true",
+                    help="time direct calls instead of replays of a CUDA graph holding one call")
     ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--batches", type=int, default=20, help="join workload: point batches per step")
     ap.add_argument("--streams", type=int, default=4,
@@ -508,12 +510,34 @@ def main():
             return api.pip_classify_slab(*a_, index=slab, **k_)
     cand_o, cand_i = d.get("cand_offsets"), d.get("cand_ids")
 
-    def step():
+    def call():
         fn(d["points"], d["poly_offsets"], d["verts"], cand_o, cand_i, out=out)
 
-    stream = torch.cuda.current_stream()
-    for _ in range(args.warmup):
-        step()
+    # a step is one replay of a CUDA graph holding one call (warm-up calls on the capture stream
+    # first, so that the library's per-stream work list exists before capture)
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            call()
+    stream.synchronize()
+    graph = None
+    per_replay = 0
+    if not args.no_graph:
+        graph = torch.cuda.CUDAGraph()
+        l0 = api.pip_launch_count()
+        with torch.cuda.graph(graph, stream=stream):
+            call()
+        per_replay = api.pip_launch_count() - l0
+
+    def step():
+        if graph is not None:
+            graph.replay()
+        else:
+            call()
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            step()
     torch.cuda.synchronize()
 
     sampler = ClockSampler(local)
@@ -523,18 +547,27 @@ def main():
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
+    # inputs that an L2 of 126 MB could hold (below 160 MB): the L2 is flushed (a 256 MB write)
+    # between timed steps, outside the events, and the step time is the mean of the per-step
+    # intervals
+    flush = None
+    if B < 160 * 10**6:
+        flush = torch.empty(256 * 2**20, dtype=torch.uint8, device="cuda")
     launches0 = api.pip_launch_count()
-    for i in range(args.steps):
-        ev0[i].record(stream)
-        step()
-        ev1[i].record(stream)
-    launches = api.pip_launch_count() - launches0
+    with torch.cuda.stream(stream):
+        for i in range(args.steps):
+            if flush is not None:
+                flush.zero_()
+            ev0[i].record(stream)
+            step()
+            ev1[i].record(stream)
+    launches = api.pip_launch_count() - launches0 + per_replay * args.steps
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
     clocks = sampler.stop()
     per = [ev0[i].elapsed_time(ev1[i]) for i in range(args.steps)]
-    total_ms = ev0[0].elapsed_time(ev1[-1])
+    total_ms = sum(per) if flush is not None else ev0[0].elapsed_time(ev1[-1])
     total_ms = max_over_ranks(dist, total_ms)
     T_all = sum_over_ranks(dist, T)
     C_all = sum_over_ranks(dist, w.n_candidates)
@@ -647,7 +680,9 @@ def main():
                                    f"{w.verts.shape[0]} vertices", "pair_tests_per_step": T,
                        "algorithmic_bytes_per_step": B, "kernel": args.kernel,
                        "tuning": list(api.pip_get_tuning()), "autotuned": autotuned,
-                       "l2": "inputs larger than L2 (no flush)"},
+                       "timing": "one CUDA-graph replay per step" if graph is not None else "direct calls",
+                       "l2": ("L2 flushed between steps (256 MB write, outside the timed intervals)"
+                              if flush is not None else "inputs larger than L2 (no flush)")},
             "points_per_s": job_rate(C_all, ms_step),
             "roofline": roof,
             "cpu_baseline": cpu,
