@@ -10,9 +10,10 @@
 // pip_bin_fill run both on one workspace.  All on the device, no host synchronisation:
 //   1. polygon bounding boxes (one warp per polygon); lane l of the warp also counts the cells
 //      of edge 2^l that the box covers, for every level l at once;
-//   2. the level (one thread): the finest cell edge 2^l at which the (polygon, cell) pairs of
-//      the boxes covering at most 64 cells fit the pair list (4 per polygon + 1024), with at
-//      most 256 larger boxes -- those go on a short list that every point tests directly;
+//   2. the level (one warp, a lane per level): the finest cell edge 2^l at which the
+//      (polygon, cell) pairs of the boxes covering at most 64 cells fit the pair list (4 per
+//      polygon + 1024), with at most 256 larger boxes -- those go on a short list that every
+//      point tests directly;
 //   3. the occupied cells in an open-addressing hash table keyed by the cell (cx, cy),
 //      cx = (x + 2^31) >> l: insert, count polygons per cell, scan, fill the per-cell lists
 //      (each entry a copy of the polygon's box, so that a point reads its cell's slot -- key,
@@ -342,7 +343,7 @@ __global__ void k_cells(const int4 *__restrict__ bb, const int32_t *__restrict__
             for (unsigned cx = cx0; cx <= cx1; ++cx) {
                 const unsigned long long key = cell_key(cx, cy);
                 unsigned long long s = hash_slot(key, hbits);
-                // the table is at most half full, so a free or matching slot is always found
+                // the table is at most a quarter full, so a free or matching slot is always found
                 for (unsigned long long it = 0; it <= hmask; ++it, s = (s + 1) & hmask) {
                     if (INSERT) {
                         const unsigned long long prev = atomicCAS(&ent[s].key, BIN_EMPTY, key);
