@@ -384,6 +384,41 @@ def run_join(args, rank, world):
     ms, clocks = res["full"]
     T_all = sum_over_ranks(dist, T)
     bin_ms = res["binning"][0]
+    # end to end: every step copies the batches' points from pinned host memory into the
+    # buffers the graph reads, replays it, and reads back the bits and the candidate CSR
+    e2e = None
+    if not args.no_e2e:
+        h_pts = [torch.from_numpy(x).pin_memory() for x in host_pts]
+        h_out = [torch.empty(o.numel(), dtype=torch.int32).pin_memory() for o in outs]
+        h_ids = [torch.empty(t_, dtype=torch.int32).pin_memory() for t_ in totals]
+        h_co = [torch.empty(P + 1, dtype=torch.int32).pin_memory() for _ in range(nb)]
+        h2d = sum(x.numel() * x.element_size() for x in h_pts)
+        d2h = sum(x.numel() * 4 for x in h_out) + sum(x.numel() * 4 for x in h_ids) + nb * 4 * (P + 1)
+
+        def e2e_step():
+            for b in range(nb):
+                d_pts[b].copy_(h_pts[b], non_blocking=True)
+            graphs["full"].replay()
+            for b in range(nb):
+                h_co[b].copy_(co[b], non_blocking=True)
+                h_ids[b].copy_(ids[b][:totals[b]], non_blocking=True)
+                h_out[b].copy_(outs[b], non_blocking=True)
+
+        n_e = max(1, min(args.e2e_steps, 5))
+        with torch.cuda.stream(stream):
+            e2e_step()
+            stream.synchronize()
+            if dist:
+                dist.barrier()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(n_e):
+                e2e_step()
+            e1.record(stream)
+            stream.synchronize()
+        e2e_ms = max_over_ranks(dist, e0.elapsed_time(e1)) / n_e
+        e2e = {"value": job_rate(T_all, e2e_ms), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(d2h), "ms_per_step": e2e_ms}
     # algorithmic bytes of a step (what any binning + classification must move, independent of
     # how it is done): the polygons' vertices read once for the index; per batch the points read
     # once and the CSR written (offsets, ids); the classification reads vertices, offsets, ids
@@ -417,7 +452,7 @@ def run_join(args, rank, world):
                              "unit": "GB/s", "frac": join_bytes / (ms / 1000.0) / 1e9 / hbm, "traffic": None,
                              "peak_source": peak_kind, "kernel": "binning + k_pip_warp + k_pip_large (whole step)",
                              "algorithmic_bytes": join_bytes, "kernel_ms": ms},
-                "e2e": None}
+                "e2e": e2e}
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
