@@ -618,10 +618,11 @@ def main():
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         n_o = max(5, min(200, args.steps))
-        e0.record(stream)
-        for _ in range(n_o):
-            other_fn(d["points"], d["poly_offsets"], d["verts"], cand_o, cand_i, out=out)
-        e1.record(stream)
+        with torch.cuda.stream(stream):   # the calls run on the stream the events are recorded on
+            e0.record(stream)
+            for _ in range(n_o):
+                other_fn(d["points"], d["poly_offsets"], d["verts"], cand_o, cand_i, out=out)
+            e1.record(stream)
         torch.cuda.synchronize()
         other_ms = e0.elapsed_time(e1) / n_o
 
@@ -648,10 +649,11 @@ def main():
         if dist:
             dist.barrier()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for _ in range(args.e2e_steps):
-            e2e_step()
-        e1.record(stream)
+        with torch.cuda.stream(stream):   # copies and calls on the stream the events are recorded on
+            e0.record(stream)
+            for _ in range(args.e2e_steps):
+                e2e_step()
+            e1.record(stream)
         torch.cuda.synchronize()
         e2e_ms = max_over_ranks(dist, e0.elapsed_time(e1)) / args.e2e_steps
         e2e = {"value": job_rate(T_all, e2e_ms), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
