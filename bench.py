@@ -326,16 +326,32 @@ def run_join(args, rank, world):
     outs = [torch.empty(cap // 32 + 1, dtype=torch.int32, device="cuda") for _ in range(nb)]
     ovf = torch.zeros(nb, dtype=torch.int32, device="cuda")
 
-    def one_pass(classify=True):
+    # pinned host buffers of the end-to-end step: the batches' points in, their bits and candidate
+    # CSR out
+    if not args.no_e2e:
+        h_pts = [torch.from_numpy(x).pin_memory() for x in host_pts]
+        h_out = [torch.empty(o.numel(), dtype=torch.int32).pin_memory() for o in outs]
+        h_ids = [torch.empty(t_, dtype=torch.int32).pin_memory() for t_ in totals]
+        h_co = [torch.empty(P + 1, dtype=torch.int32).pin_memory() for _ in range(nb)]
+
+    def one_pass(classify=True, io=False):
         api.bin_index(d_po, d_v, index=index, stream=stream)
         for s_ in streams:
             s_.wait_stream(stream)
         for b in range(nb):
             s_, q_ = streams[b % ns], probes[b % ns]
+            if io:   # this batch's points from the host, on the batch's stream
+                with torch.cuda.stream(s_):
+                    d_pts[b].copy_(h_pts[b], non_blocking=True)
             api.pip_bin_probe_count(d_pts[b], index, P, probe=q_, cand_offsets=co[b], d_total=tot[b], stream=s_)
             api.pip_bin_probe_fill(d_pts[b], index, P, q_, co[b], ids[b], d_overflow=ovf[b:b + 1], stream=s_)
             if classify:
                 api.pip_classify(d_pts[b], d_po, d_v, co[b], ids[b], out=outs[b], stream=s_)
+            if io:   # its bits and candidate lists back, while the other streams compute
+                with torch.cuda.stream(s_):
+                    h_co[b].copy_(co[b], non_blocking=True)
+                    h_ids[b].copy_(ids[b][:totals[b]], non_blocking=True)
+                    h_out[b].copy_(outs[b], non_blocking=True)
         for s_ in streams:
             stream.wait_stream(s_)
 
@@ -359,6 +375,11 @@ def run_join(args, rank, world):
             one_pass(cls)
         per_replay[name] = api.pip_launch_count() - l0
         graphs[name] = g
+    g_e2e = None
+    if not args.no_e2e:
+        g_e2e = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g_e2e, stream=stream):
+            one_pass(True, io=True)
     res = {}
     for name, g in graphs.items():
         with torch.cuda.stream(stream):
@@ -384,25 +405,16 @@ def run_join(args, rank, world):
     ms, clocks = res["full"]
     T_all = sum_over_ranks(dist, T)
     bin_ms = res["binning"][0]
-    # end to end: every step copies the batches' points from pinned host memory into the
-    # buffers the graph reads, replays it, and reads back the bits and the candidate CSR
+    # end to end: one replay of a graph in which every batch's stream copies its points from
+    # pinned host memory, bins and classifies them, and copies its bits and candidate CSR back,
+    # so that copies overlap the other batches' kernels
     e2e = None
-    if not args.no_e2e:
-        h_pts = [torch.from_numpy(x).pin_memory() for x in host_pts]
-        h_out = [torch.empty(o.numel(), dtype=torch.int32).pin_memory() for o in outs]
-        h_ids = [torch.empty(t_, dtype=torch.int32).pin_memory() for t_ in totals]
-        h_co = [torch.empty(P + 1, dtype=torch.int32).pin_memory() for _ in range(nb)]
+    if g_e2e is not None:
         h2d = sum(x.numel() * x.element_size() for x in h_pts)
         d2h = sum(x.numel() * 4 for x in h_out) + sum(x.numel() * 4 for x in h_ids) + nb * 4 * (P + 1)
 
         def e2e_step():
-            for b in range(nb):
-                d_pts[b].copy_(h_pts[b], non_blocking=True)
-            graphs["full"].replay()
-            for b in range(nb):
-                h_co[b].copy_(co[b], non_blocking=True)
-                h_ids[b].copy_(ids[b][:totals[b]], non_blocking=True)
-                h_out[b].copy_(outs[b], non_blocking=True)
+            g_e2e.replay()
 
         n_e = max(1, min(args.e2e_steps, 5))
         with torch.cuda.stream(stream):
