@@ -14,9 +14,11 @@ import torch
 
 from . import _lib
 
-__all__ = ["pip_classify", "pip_classify_exact", "pip_classify_paper", "pip_classify_slab", "slab_index", "quantize_lonlat", "pip_classify_noalloc", "pip_bin_count", "pip_bin_fill", "bin_join",
-           "pip_set_tuning", "pip_get_tuning", "pip_get_stats", "pip_reset_stats", "pip_launch_count", "pip_set_verify", "pip_validate",
-           "out_words", "to_device"]
+__all__ = ["pip_classify", "pip_classify_exact", "pip_classify_paper", "pip_classify_slab", "slab_index",
+           "quantize_lonlat", "pip_classify_noalloc", "bin_index", "probe_workspace", "pip_bin_probe_count",
+           "pip_bin_probe_fill", "pip_bin_count", "pip_bin_fill", "bin_workspace", "bin_join",
+           "pip_set_tuning", "pip_get_tuning", "pip_get_stats", "pip_reset_stats", "pip_launch_count",
+           "pip_set_verify", "pip_validate", "out_words", "to_device"]
 
 
 def _ptr(t):
