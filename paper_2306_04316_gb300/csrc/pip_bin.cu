@@ -520,18 +520,19 @@ __device__ __forceinline__ int warp_sort32(int v, int lane)
 // V[0..n) sorted ascending by threads t0, t0 + nt, ... of a group that `sync` synchronises: the
 // same network over the next power of two, positions n and beyond counting as +infinity (a
 // comparator never moves one of them below n, so they are never touched).
-template <typename Sync>
-__device__ void bitonic_sort(int *V, int n, int t0, int nt, Sync sync)
+// Idx: int for the shared-memory sorts, long long for lists in global memory (up to 2^31 ids).
+template <typename Idx, typename Sync>
+__device__ void bitonic_sort(int *V, Idx n, int t0, int nt, Sync sync)
 {
-    int P2 = 1;
+    Idx P2 = 1;
     while (P2 < n) P2 <<= 1;
-    for (int kk = 2; kk <= P2; kk <<= 1) {
-        for (int j = kk >> 1; j > 0; j >>= 1) {
-            const int lj = __ffs(j) - 1;
-            for (int t = t0; t < (P2 >> 1); t += nt) {
-                const int blk = t >> lj, r = t & (j - 1);
-                const int i = (blk << (lj + 1)) + r;
-                const int q = j == (kk >> 1) ? (blk << (lj + 1)) + kk - 1 - r : i + j;
+    for (Idx kk = 2; kk <= P2; kk <<= 1) {
+        for (Idx j = kk >> 1; j > 0; j >>= 1) {
+            const int lj = __ffsll((long long)j) - 1;
+            for (Idx t = t0; t < (P2 >> 1); t += nt) {
+                const Idx blk = t >> lj, r = t & (j - 1);
+                const Idx i = (blk << (lj + 1)) + r;
+                const Idx q = j == (kk >> 1) ? (blk << (lj + 1)) + kk - 1 - r : i + j;
                 if (q < n) {
                     const int x = V[i], y = V[q];
                     if (x > y) {
@@ -623,7 +624,7 @@ __global__ void __launch_bounds__(256) k_seg_sort_medium(const int32_t *__restri
         } else {
             for (int i = lane; i < n; i += 32) wv[i] = ids[a + i];
             __syncwarp();
-            bitonic_sort(wv, (int)n, lane, 32, [] { __syncwarp(); });
+            bitonic_sort<int>(wv, (int)n, lane, 32, [] { __syncwarp(); });
             for (int i = lane; i < n; i += 32) ids[a + i] = wv[i];
             __syncwarp();
         }
@@ -646,10 +647,10 @@ __global__ void __launch_bounds__(256) k_seg_sort_long(const int32_t *__restrict
         if (n <= SORT_CTA_SMEM) {
             for (int i = tid; i < n; i += 256) s_v[i] = ids[a + i];
             __syncthreads();
-            bitonic_sort(s_v, (int)n, tid, 256, [] { __syncthreads(); });
+            bitonic_sort<int>(s_v, (int)n, tid, 256, [] { __syncthreads(); });
             for (int i = tid; i < n; i += 256) ids[a + i] = s_v[i];
         } else {
-            bitonic_sort(ids + a, (int)n, tid, 256, [] { __syncthreads(); });
+            bitonic_sort<long long>(ids + a, n, tid, 256, [] { __syncthreads(); });
         }
         __syncthreads();
     }
