@@ -485,7 +485,7 @@ const char *pip_status_str(int code)
 
 int pip_last_cuda_error(void) { return g_last_cuda; }
 
-int pip_version(void) { return 102; }
+int pip_version(void) { return 103; }
 
 uint64_t pip_launch_count(void) { return g_launches.load(); }
 
