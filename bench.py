@@ -286,6 +286,34 @@ def run_reference(args, rank, world):
     return 0
 
 
+def arithmetic_of(w):
+    """The arithmetic the filtered kernels use on this workload, from the polygons' boxes: exact
+    int32 for boxes below 2^30 with width x height below 2^30, exact int64 for boxes below 2^31,
+    FP32 (with an exact integer recheck) above and for polygons of more than 256 vertices;
+    "i32+i64" when both integer kinds occur, and so on."""
+    import numpy as np
+    po = w.poly_offsets.astype(np.int64)
+    m = np.diff(po)
+    keep = m > 0
+    if not keep.any():
+        return "i32"
+    v = w.verts.astype(np.int64)
+    starts = po[:-1][keep]
+    W_ = np.maximum.reduceat(v[:, 0], starts) - np.minimum.reduceat(v[:, 0], starts)
+    H_ = np.maximum.reduceat(v[:, 1], starts) - np.minimum.reduceat(v[:, 1], starts)
+    i32 = (W_ < 2**30) & (H_ < 2**30) & (W_ * H_ < 2**30)
+    i64 = ~i32 & (W_ < 2**31) & (H_ < 2**31)
+    large = (m[keep] > 256)
+    kinds = []
+    if (i32 & ~large).any():
+        kinds.append("i32")
+    if (i64 & ~large).any():
+        kinds.append("i64")
+    if ((~i32 & ~i64) | large).any():   # large polygons always take the FP32 filter
+        kinds.append("f32")
+    return "+".join(kinds)
+
+
 def run_join(args, rank, world):
     """Spatial join: 100k footprint polygons against 20 batches of 10M clustered points; one
     step = one replay of a CUDA graph that bins and classifies all 20 batches."""
@@ -451,7 +479,8 @@ def run_join(args, rank, world):
     if rank == 0:
         line = {"metric": METRIC, "value": job_rate(T_all, ms), "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-                "vs_baseline": None, "dtype": "f32+i64", "data": "synthetic",
+                "vs_baseline": None, "dtype": arithmetic_of(W.Workload("join", host_pts[0][:1], po, v)),
+                "data": "synthetic",
                 "config": {"workload": f"join: {P} polygons x {nb} batches of {n_pts} clustered points, "
                                        f"{C} candidates from GPU binning, one CUDA-graph replay per step "
                                        f"({ns} streams)",
@@ -723,7 +752,8 @@ def main():
         line = {
             "metric": METRIC, "value": job_rate(T_all, ms_step), "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32+i64" if args.kernel == "filtered" else "i64",
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": arithmetic_of(w) if args.kernel == "filtered" else "i64",
             "data": "synthetic",
             "config": {"workload": f"{w.name}: {w.n_polys} polygons, {w.n_candidates} candidates, "
                                    f"{w.verts.shape[0]} vertices", "pair_tests_per_step": T,
