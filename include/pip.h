@@ -27,13 +27,18 @@
  *   cand_offsets, cand_ids
  *                 device CSR of candidate points: polygon k's candidates are
  *                 cand_ids[cand_offsets[k] .. cand_offsets[k+1]) (cand_offsets
- *                 non-decreasing, cand_offsets[0] = 0, ids in [0, n_points)).  Both NULL
- *                 selects DENSE mode: every point against every polygon.
+ *                 non-decreasing and >= 0, ids in [0, n_points)).  Offsets are absolute
+ *                 indices into cand_ids and out_bits, so a call may cover a range of a larger
+ *                 CSR (pointers to poly_offsets + p0 and cand_offsets + p0 with n_polys = p1 - p0);
+ *                 normally cand_offsets[0] = 0.  Both NULL selects DENSE mode: every point
+ *                 against every polygon.
  *   out_bits      device, uint32.  CSR mode: ceil(C / 32) words, C = cand_offsets[n_polys];
  *                 bit c (word c >> 5, bit c & 31, LSB first) = "point cand_ids[c] is inside
  *                 the polygon that owns candidate c".  Dense mode: n_polys * W words,
  *                 W = ceil(n_points / 32); bit k*32*W + j = "point j is inside polygon k".
- *                 Every word is overwritten (bits past the last candidate are 0).
+ *                 Every bit of [cand_offsets[0], C) is written and the bits of the final word
+ *                 past C are 0; bits below cand_offsets[0] are left as they are (dense mode:
+ *                 every word is written).
  *   stream        a cudaStream_t passed as void* (NULL = the legacy default stream).
  *
  * Ownership and errors: the caller owns every buffer.  Calls are asynchronous on `stream`
@@ -77,8 +82,12 @@ typedef struct pip_stats {
                                   error bound) differs from the exact 64/128-bit test; 0 means the
                                   filter was sound on every pair it trusted */
     uint64_t verified_pairs;   /* verification mode only: trusted decisions that were rechecked */
-    uint64_t wait_timeouts;    /* CTAs whose bounded wait for a bulk copy of edges gave up (their
-                                  bits are then unreliable; never expected, always 0 in tests) */
+    uint64_t wait_timeouts;    /* large-polygon CTAs whose bounded wait for a bulk copy of edges
+                                  gave up (such a CTA stops using its shared tile buffer and decides
+                                  its remaining pairs exactly from global memory, so the bits stay
+                                  exact, only slower), plus warps of the small-polygon kernel whose
+                                  loop guard ended their work early (their bits are then incomplete).
+                                  Never expected; 0 in every test */
 } pip_stats;
 
 /*
@@ -183,7 +192,9 @@ int pip_classify_slab(const int32_t *points, int64_t n_points,
  *   make that first call before any stream capture that includes this entry point.
  *   Every call shares the one array and clears its header on `stream` first; calls whose
  *   work overlaps on the GPU (different streams, or different host threads) race on it and
- *   must be serialised by the caller.  pip_get_stats counters are not updated.
+ *   must be serialised by the caller.  Its statistics counters live in the same array (they are
+ *   not cleared per call); pip_get_stats adds them to pip_classify's, and pip_reset_stats
+ *   clears both.
  */
 #define PIP_NOALLOC_MAX_POLYS 65536
 int pip_classify_noalloc(const int32_t *points, int64_t n_points,
@@ -269,6 +280,21 @@ int pip_bin_fill(const int32_t *points, int64_t n_points,
 int pip_set_tuning(int32_t edge_tile, int32_t pts_per_thread, int32_t ctas_per_sm);
 int pip_get_tuning(int32_t *edge_tile, int32_t *pts_per_thread, int32_t *ctas_per_sm);
 
+/*
+ * Tuning of pip_classify's small-polygon kernel (the autotuner's hook; not in the paper; the
+ * bits never depend on it).
+ *   kernel       0 (default) = lockstep kernel: every candidate walks its polygon's edges in
+ *                rounds of 32 consecutive candidates; 1 = compacting kernel: the candidates of a
+ *                slice that lie inside their polygon's box are packed together before the edge
+ *                walk, and each slice's loads are issued one slice ahead; -1 keeps the value
+ *   slice        compacting kernel: candidates per slice, 128 or 256 (default); 0 keeps it
+ *   ctas_per_sm  compacting kernel: resident CTAs per SM, 1..16, 0 = as many as fit (default);
+ *                -1 keeps it
+ * Applies to later calls on every device; PIP_ERR_INVALID for an out-of-range value.
+ */
+int pip_set_small_tuning(int32_t kernel, int32_t slice, int32_t ctas_per_sm);
+int pip_get_small_tuning(int32_t *kernel, int32_t *slice, int32_t *ctas_per_sm);
+
 /* Statistics (device counters of the current device).  pip_get_stats copies them to the
  * host with a synchronous copy: call it after the work of interest has completed. */
 int pip_get_stats(pip_stats *out);
@@ -280,7 +306,7 @@ int pip_reset_stats(void);
  * vertices and ids); the check reads poly_offsets, cand_offsets and at most n_cand_ids ids,
  * never past them.  Writes *d_status (device int32): 0 if valid, else a bit mask:
  *   1  poly_offsets negative or decreasing        2  cand_offsets decreasing or
- *                                                    cand_offsets[0] != 0
+ *                                                    negative
  *   4  a candidate id outside [0, n_points)       8  poly_offsets[n_polys] > n_verts
  *  16  cand_offsets[n_polys] > n_cand_ids
  * A call that passes makes pip_classify read only inside the given arrays.
@@ -299,6 +325,16 @@ int pip_validate(const int32_t *points, int64_t n_points,
  * Returns PIP_OK, or PIP_ERR_INVALID for another value.
  */
 int pip_set_verify(int32_t on);
+
+/*
+ * pip_xor_words -- dst[i] ^= src[i] for i < n_words (device uint32 arrays, 4-byte aligned), on
+ * `stream`.  The parity reduction (step 7) across partitions of a polygon's edges: when a
+ * classification is split by edges (each part a chain of the polygon's edges closed through its
+ * first vertex, so that the added closing edges cancel in pairs), the inside bit is the XOR of
+ * the parts' bits, and multi-GPU callers combine the parts' outputs with this call after an
+ * all-gather.  Returns PIP_OK or PIP_ERR_*.
+ */
+int pip_xor_words(uint32_t *dst, const uint32_t *src, int64_t n_words, void *stream);
 
 /* Human-readable name of a PIP_* status code. */
 const char *pip_status_str(int code);

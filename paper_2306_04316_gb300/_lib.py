@@ -71,6 +71,8 @@ _SIGS = {
     "pip_bin_fill": ([_P, _I64, _P, _P, _I32, _P, ctypes.c_size_t, _P, _P, _I64, _P, _P], ctypes.c_int),
     "pip_set_tuning": ([_I32, _I32, _I32], ctypes.c_int),
     "pip_get_tuning": ([_P, _P, _P], ctypes.c_int),
+    "pip_set_small_tuning": ([_I32, _I32, _I32], ctypes.c_int),
+    "pip_get_small_tuning": ([_P, _P, _P], ctypes.c_int),
     "pip_get_stats": ([ctypes.POINTER(PipStats)], ctypes.c_int),
     "pip_reset_stats": ([], ctypes.c_int),
     "pip_validate": ([_P, _I64, _P, _P, _I32, _I64, _P, _P, _I64, _P, _P], ctypes.c_int),
@@ -79,6 +81,7 @@ _SIGS = {
     "pip_version": ([], ctypes.c_int),
     "pip_launch_count": ([], ctypes.c_uint64),
     "pip_set_verify": ([_I32], ctypes.c_int),
+    "pip_xor_words": ([_P, _P, _I64, _P], ctypes.c_int),
 }
 
 

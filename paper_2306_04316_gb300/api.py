@@ -17,8 +17,8 @@ from . import _lib
 __all__ = ["pip_classify", "pip_classify_exact", "pip_classify_paper", "pip_classify_slab", "slab_index",
            "quantize_lonlat", "pip_classify_noalloc", "bin_index", "probe_workspace", "pip_bin_probe_count",
            "pip_bin_probe_fill", "pip_bin_count", "pip_bin_fill", "bin_workspace", "bin_join",
-           "pip_set_tuning", "pip_get_tuning", "pip_get_stats", "pip_reset_stats", "pip_launch_count",
-           "pip_set_verify", "pip_validate", "out_words", "to_device"]
+           "pip_set_tuning", "pip_get_tuning", "pip_set_small_tuning", "pip_get_small_tuning", "pip_get_stats", "pip_reset_stats", "pip_launch_count",
+           "pip_set_verify", "pip_validate", "pip_xor_words", "out_words", "to_device"]
 
 
 def _ptr(t):
@@ -261,6 +261,29 @@ def pip_get_tuning():
     v = [ctypes.c_int32() for _ in range(3)]
     _lib.check("pip_get_tuning", _lib.load().pip_get_tuning(*[ctypes.byref(x) for x in v]))
     return tuple(x.value for x in v)
+
+
+def pip_set_small_tuning(kernel=-1, slice=0, ctas_per_sm=-1):
+    """Small-polygon kernel: 1 = compacting, 0 = lockstep rounds; candidates per slice (128,
+    256); resident CTAs per SM (0 = as many as fit).  -1 / 0 keep a value."""
+    _lib.check("pip_set_small_tuning", _lib.load().pip_set_small_tuning(kernel, slice, ctas_per_sm))
+
+
+def pip_get_small_tuning():
+    v = [ctypes.c_int32() for _ in range(3)]
+    _lib.check("pip_get_small_tuning", _lib.load().pip_get_small_tuning(*[ctypes.byref(x) for x in v]))
+    return tuple(x.value for x in v)
+
+
+def pip_xor_words(dst, src, stream=None):
+    """dst ^= src on the device (int32 tensors of the same length; ``pip_xor_words``)."""
+    for t, n in ((dst, "dst"), (src, "src")):
+        if not t.is_cuda or t.dtype != torch.int32 or not t.is_contiguous():
+            raise ValueError(f"{n} must be a contiguous int32 CUDA tensor")
+    if dst.numel() != src.numel():
+        raise ValueError("dst and src must have the same length")
+    _lib.check("pip_xor_words", _lib.load().pip_xor_words(_ptr(dst), _ptr(src), dst.numel(), _stream(stream)))
+    return dst
 
 
 def pip_get_stats() -> dict:

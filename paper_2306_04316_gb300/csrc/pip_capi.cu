@@ -1,5 +1,6 @@
 // C ABI of libpip (declared in include/pip.h): argument checks, the per-device
 // workspace, tuning state, statistics and the opt-in device-side validation.
+#include <algorithm>
 #include <atomic>
 #include <climits>
 #include <cstring>
@@ -30,13 +31,10 @@ std::atomic<int> g_ctas{3};
 std::atomic<int> g_ppt{4};
 std::atomic<unsigned long long> g_launches{0};
 std::atomic<int> g_verify{0};
+std::atomic<int> g_small_kernel{0};
+std::atomic<int> g_small_slice{256};
+std::atomic<int> g_small_ctas{0};
 thread_local int g_last_cuda = 0;
-
-int cuda_fail(cudaError_t e)
-{
-    g_last_cuda = (int)e;
-    return PIP_ERR_CUDA;
-}
 
 bool capturing(cudaStream_t s)
 {
@@ -134,8 +132,18 @@ ClassifyArgs make_args(const int32_t *points, int64_t n_points, const int32_t *p
 
 void pipdev::note_launch(int n) { g_launches.fetch_add((unsigned long long)n); }
 
+int pipdev::cuda_fail(cudaError_t e)
+{
+    g_last_cuda = (int)e;
+    return PIP_ERR_CUDA;
+}
+
 namespace pipdev {
-Tuning current_tuning() { return Tuning{g_edge_tile.load(), g_ppt.load(), g_ctas.load(), g_verify.load()}; }
+Tuning current_tuning()
+{
+    return Tuning{g_edge_tile.load(),   g_ppt.load(),         g_ctas.load(),      g_verify.load(),
+                  g_small_kernel.load(), g_small_slice.load(), g_small_ctas.load()};
+}
 }  // namespace pipdev
 
 extern "C" {
@@ -273,6 +281,26 @@ int pip_set_tuning(int32_t edge_tile, int32_t pts_per_thread, int32_t ctas_per_s
     return PIP_OK;
 }
 
+int pip_set_small_tuning(int32_t kernel, int32_t slice, int32_t ctas_per_sm)
+{
+    if (kernel < -1 || kernel > 1) return PIP_ERR_INVALID;
+    if (slice != 0 && slice != 128 && slice != 256) return PIP_ERR_INVALID;
+    if (ctas_per_sm < -1 || ctas_per_sm > 16) return PIP_ERR_INVALID;
+    if (kernel >= 0) g_small_kernel.store(kernel);
+    if (slice) g_small_slice.store(slice);
+    if (ctas_per_sm >= 0) g_small_ctas.store(ctas_per_sm);
+    return PIP_OK;
+}
+
+int pip_get_small_tuning(int32_t *kernel, int32_t *slice, int32_t *ctas_per_sm)
+{
+    if (!kernel || !slice || !ctas_per_sm) return PIP_ERR_NULL;
+    *kernel = g_small_kernel.load();
+    *slice = g_small_slice.load();
+    *ctas_per_sm = g_small_ctas.load();
+    return PIP_OK;
+}
+
 int pip_get_tuning(int32_t *edge_tile, int32_t *pts_per_thread, int32_t *ctas_per_sm)
 {
     if (!edge_tile || !pts_per_thread || !ctas_per_sm) return PIP_ERR_NULL;
@@ -291,6 +319,8 @@ int pip_get_stats(pip_stats *out)
     unsigned long long h[ST_COUNT];
     cudaError_t e = cudaMemcpy(h, ds->stats, sizeof h, cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return cuda_fail(e);
+    const int en = noalloc_stats(h, false);   // pip_classify_noalloc's own counters
+    if (en) return cuda_fail((cudaError_t)en);
     out->candidates = h[ST_CANDIDATES];
     out->bbox_rejects = h[ST_BBOX_REJECTS];
     out->fallback_points = h[ST_FALLBACK_POINTS];
@@ -314,7 +344,10 @@ int pip_reset_stats(void)
     int rc = device_state(nullptr, &ds);
     if (rc != PIP_OK) return rc;
     cudaError_t e = cudaMemset(ds->stats, 0, ST_COUNT * sizeof(unsigned long long));
-    return e == cudaSuccess ? PIP_OK : cuda_fail(e);
+    if (e != cudaSuccess) return cuda_fail(e);
+    unsigned long long h[ST_COUNT] = {0};
+    const int en = noalloc_stats(h, true);
+    return en == 0 ? PIP_OK : cuda_fail((cudaError_t)en);
 }
 
 int pip_validate(const int32_t *points, int64_t n_points, const int32_t *poly_offsets,
@@ -468,6 +501,20 @@ int pip_bin_probe_fill(const int32_t *points, int64_t n_points, const void *inde
     return e == 0 ? PIP_OK : cuda_fail((cudaError_t)e);
 }
 
+int pip_xor_words(uint32_t *dst, const uint32_t *src, int64_t n_words, void *stream)
+{
+    if (n_words < 0) return PIP_ERR_SIZE;
+    if (n_words > 0 && (!dst || !src)) return PIP_ERR_NULL;
+    if (misaligned(dst, 4) || misaligned(src, 4)) return PIP_ERR_ALIGN;
+    if (n_words == 0) return PIP_OK;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    DeviceState *ds = nullptr;
+    int rc = device_state(s, &ds);
+    if (rc != PIP_OK) return rc;
+    const int e = launch_xor_words(dst, src, n_words, ds->n_sm, s);
+    return e == 0 ? PIP_OK : cuda_fail((cudaError_t)e);
+}
+
 const char *pip_status_str(int code)
 {
     switch (code) {
@@ -485,7 +532,7 @@ const char *pip_status_str(int code)
 
 int pip_last_cuda_error(void) { return g_last_cuda; }
 
-int pip_version(void) { return 103; }
+int pip_version(void) { return 104; }
 
 uint64_t pip_launch_count(void) { return g_launches.load(); }
 
@@ -511,7 +558,7 @@ __global__ void k_validate(ClassifyArgs a, long long n_verts, long long n_cand_i
     }
     if (tid == 0 && (long long)a.poly_offsets[a.n_polys] > n_verts) bad |= 8;
     if (a.cand_offsets) {
-        if (tid == 0 && a.cand_offsets[0] != 0) bad |= 2;
+        if (tid == 0 && a.cand_offsets[0] < 0) bad |= 2;
         long long C = a.cand_offsets[a.n_polys];
         if (C > n_cand_ids) {
             if (tid == 0) bad |= 16;
@@ -523,6 +570,37 @@ __global__ void k_validate(ClassifyArgs a, long long n_verts, long long n_cand_i
         }
     }
     if (bad) atomicOr(status, bad);
+}
+
+// dst[i] ^= src[i]: the parity reduction of step 7 across edge partitions (16-byte words where
+// both arrays allow it, a grid-stride loop over 32-bit words otherwise)
+__global__ void k_xor_words(uint32_t *dst, const uint32_t *src, long long n)
+{
+    const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long nthr = (long long)gridDim.x * blockDim.x;
+    const bool vec = ((reinterpret_cast<uintptr_t>(dst) | reinterpret_cast<uintptr_t>(src)) & 15) == 0;
+    long long done = 0;
+    if (vec) {
+        const long long n4 = n / 4;
+        uint4 *d4 = reinterpret_cast<uint4 *>(dst);
+        const uint4 *s4 = reinterpret_cast<const uint4 *>(src);
+        for (long long i = tid; i < n4; i += nthr) {
+            uint4 a = d4[i];
+            const uint4 b = s4[i];
+            a.x ^= b.x; a.y ^= b.y; a.z ^= b.z; a.w ^= b.w;
+            d4[i] = a;
+        }
+        done = n4 * 4;
+    }
+    for (long long i = done + tid; i < n; i += nthr) dst[i] ^= src[i];
+}
+
+int launch_xor_words(uint32_t *dst, const uint32_t *src, long long n, int n_sm, cudaStream_t stream)
+{
+    const long long blocks = std::min<long long>((long long)n_sm * 4, (n / 4 + 255) / 256 + 1);
+    k_xor_words<<<(int)std::max(1LL, blocks), 256, 0, stream>>>(dst, src, n);
+    note_launch();
+    return (int)cudaGetLastError();
 }
 
 int launch_validate(const ClassifyArgs &a, long long n_verts, long long n_cand_ids, int *d_status, int grid,

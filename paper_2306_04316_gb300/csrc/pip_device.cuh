@@ -25,7 +25,7 @@ enum StatIdx {
     ST_EXACT_CANDIDATES = 4,
     ST_FILTER_ERRORS = 5,     // verification mode: fast-path decisions that the exact test contradicts
     ST_VERIFIED = 6,          // verification mode: fast-path decisions checked
-    ST_WAIT_TIMEOUTS = 7,     // bounded waits on an asynchronous copy that gave up (never expected)
+    ST_WAIT_TIMEOUTS = 7,     // bounded waits (or loop guards) in a kernel that gave up (never expected)
     ST_COUNT = 8
 };
 

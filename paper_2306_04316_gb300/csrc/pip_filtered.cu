@@ -58,7 +58,8 @@
 // k_pip_large -- the listed polygons.  Work items (polygon, block of 256*PPT candidates,
 //   slice of edges) are taken from the list by atomic counters; the CTA streams the slice
 //   through shared memory in tiles of T edges (each tile's vertices by one bulk copy of the
-//   tensor memory accelerator, completed on an mbarrier with a bounded wait), each tile framed
+//   tensor memory accelerator, completed on an mbarrier with a bounded wait; a CTA whose wait gives
+//   up decides the rest of its pairs exactly from global memory), each tile framed
 //   by the union of its vertices
 //   and the block's candidate points (records scaled per edge by a power of two, so that one
 //   uniform test flags the uncertain FP32 signs), and XORs the partial parities into the output
@@ -67,9 +68,11 @@
 //   Its last CTA empties the list for the next call.  With more large polygons than the list
 //   holds, it falls back to a scan over all polygons.
 #include <algorithm>
+#include <mutex>
 #include <type_traits>
 
 #include "pip_device.cuh"
+#include "pip_edge.cuh"
 #include "pip_launch.h"
 
 namespace pipdev {
@@ -77,85 +80,14 @@ namespace pipdev {
 // large-polygon kernel geometry
 constexpr int LG_THREADS = 256;
 
-// c' = s (X_i d_y - Y_i d_x) rounded to FP32 (s = sign(d_y)).
-__device__ __forceinline__ float edge_c(int2 ri, long long dx, long long dy, int ox, int oy, int wide)
-{
-    const long long X = (long long)ri.x - ox, Y = (long long)ri.y - oy;
-    float c;
-    if (!wide) {
-        c = __ll2float_rn(X * dy - Y * dx);              // |X dy|, |Y dx| < 2^61: exact int64
-    } else {
-        c = __double2float_rn(__dmul_rn((double)X, (double)dy) - __dmul_rn((double)Y, (double)dx));
-    }
-    return dy > 0 ? c : -c;
-}
-
-// Edge record of a frame 2^30 or more wide (int64 and double arithmetic; rare, out of line).
-__device__ __noinline__ float4 wide_record(int2 ri, int2 rj, int ox, int oy)
-{
-    const long long dx = (long long)rj.x - ri.x, dy = (long long)rj.y - ri.y;
-    const float c = dy == 0 ? 0.f : edge_c(ri, dx, dy, ox, oy, 1);
-    return dy > 0 ? make_float4(c, __ll2float_rn(dy), __ll2float_rn(dx), __int_as_float(rj.y))
-                  : make_float4(c, __ll2float_rn(-dy), __ll2float_rn(-dx), __int_as_float(rj.y));
-}
-
-// Exact parity of p over the edges e0..e1-1 of staged vertices v, edge e running from v[e]
-// to v[e + 1], or to v[e0] for the last edge when `wrap`.  Rare path: kept out of line.
-__device__ __noinline__ int exact_parity(const int2 *v, int e0, int e1, bool wrap, int2 p)
-{
-    int parity = 0;
-    for (int e = e0; e < e1; ++e) {
-        const int nx = (wrap && e + 1 == e1) ? e0 : e + 1;
-        const int2 ri = v[e], rj = v[nx];
-        if ((ri.y > p.y) != (rj.y > p.y)) parity ^= exact_edge_counts(p.x, p.y, ri.x, ri.y, rj.x, rj.y);
-    }
-    return parity;
-}
-
-// Exact parity of the point (px, py) over the same edges, computed by the 32 lanes of a warp
-// together (lane l takes edges e0 + l, e0 + l + 32, ...); every lane returns it.  All lanes must
-// call it.  The rare recheck of one lane's candidate over a large polygon's tile then costs its
-// warp about (e1 - e0) / 32 exact tests instead of e1 - e0.  (The small-polygon kernel keeps the
-// per-lane exact_parity: its polygons have at most 256 edges, and the warp-wide form there
-// measured more instructions on the footprint batch, whose polygons never take this path.)
-__device__ __forceinline__ int warp_exact_parity(const int2 *v, int e0, int e1, bool wrap, int px, int py, int lane)
-{
-    int part = 0;
-    for (int e = e0 + lane; e < e1; e += 32) {
-        const int nx = (wrap && e + 1 == e1) ? e0 : e + 1;
-        const int2 ri = v[e], rj = v[nx];
-        if ((ri.y > py) != (rj.y > py)) part ^= exact_edge_counts(px, py, ri.x, ri.y, rj.x, rj.y);
-    }
-    return __popc(__ballot_sync(FULL, part)) & 1;
-}
-
 // =============================================================================================
 // k_pip_warp -- small polygons; every warp works on its own runs of consecutive polygons
 // =============================================================================================
 
-// Bound factor of the FP32 records: rounding the four record inputs, the product Y d_x and the
-// fused X d_y - Y d_x, then P_x, P_y and the two per-pair fused operations, costs at most
-// 5u|X d_y| + 6u|Y d_x| + 4u|P_x d_y| + 3u|P_y d_x| (+ O(u^2)) <= 12u (M_x H + M_y W), with H, W
-// the polygon's height and width (>= |d_y|, |d_x| of every edge).
-constexpr float PM_BOUND_K = 7.748603820800781e-07f;     // 13 * 2^-24 (exact in FP32)
 constexpr int WP_THREADS = 128;     // 4 independent warps per CTA
 constexpr int WP_CTAS = 5;          // CTAs per SM (shared memory: 4 x 9.8 KB per CTA)
-constexpr int WP_V = 256;           // vertices of a run (and most vertices of a small polygon)
 constexpr int WP_R = 8;             // candidate rounds of 32 per slice
 constexpr int WP_C = 32 * WP_R;     // candidates of a slice
-constexpr long long LARGE_W = 1LL << 18;   // (candidates x vertices) above which a polygon is large
-// Arithmetic of a polygon's pair tests: exact int32 when its box is small enough that every
-// value fits (width, height < 2^30 and width * height < 2^30); exact int64 products of int32
-// differences when the box is below 2^31 on both sides; else the FP32 filter, with int64/double
-// records when the box is 2^30 or more from its centre.
-constexpr int MODE_INT32 = 0, MODE_INT64 = 1, MODE_FP32 = 2, MODE_WIDE = 3;
-
-// A polygon goes to k_pip_large when it has more vertices than a run holds or more
-// (candidate, edge) pairs than one warp should walk.
-__device__ __forceinline__ bool is_large_polygon(long long m, long long n)
-{
-    return m > WP_V || m * n > LARGE_W;
-}
 
 struct __align__(16) WarpSmem {
     float4 rec[WP_V];               // edge records of the run (int32, int64 or FP32, per polygon)
@@ -167,62 +99,6 @@ struct __align__(16) WarpSmem {
     unsigned char sp[WP_C];         // first candidate slot of a polygon -> chunk polygon
     unsigned char vp[WP_V];         // vertex -> chunk polygon
 };
-
-// Sets exactly the bits `mask` of *word to `bits` (other bits untouched, no zero-fill needed).
-__device__ __forceinline__ void masked_store(uint32_t *word, unsigned mask, unsigned bits)
-{
-    if (mask == 0xffffffffu) {
-        *word = bits;
-    } else if (mask) {
-        atomicAnd(word, ~mask | bits);
-        atomicOr(word, bits & mask);
-    }
-}
-
-__device__ __forceinline__ unsigned range_mask(int lo, int hi)   // bits [lo, hi), 0 <= lo <= hi <= 32
-{
-    return (hi >= 32 ? 0xffffffffu : ((1u << hi) - 1u)) & ~((1u << lo) - 1u);
-}
-
-// Bits [c0, c1) of the output to 0, by the 32 lanes of a warp.
-__device__ __forceinline__ void zero_bits(uint32_t *out, long long c0, long long c1, int lane)
-{
-    if (c1 <= c0) return;
-    const long long w0 = c0 >> 5, w1 = (c1 + 31) >> 5;
-    for (long long wd = w0 + lane; wd < w1; wd += 32) {
-        const int lo = (int)(max(c0, wd * 32) - wd * 32), hi = (int)(min(c1, wd * 32 + 32) - wd * 32);
-        masked_store(out + wd, range_mask(lo, hi), 0u);
-    }
-}
-
-// 16-byte shared-memory load at a 32-bit shared address.
-__device__ __forceinline__ int4 lds128(unsigned addr)
-{
-    int4 v;
-    asm volatile("ld.shared.v4.s32 {%0, %1, %2, %3}, [%4];\n"
-                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "r"(addr));
-    return v;
-}
-
-// Integer record of the edge ri -> rj for the exact int32 test (origin-free):
-// x + p_x y + p_y z = -sign(d_y) det modulo 2^32, w = y_j.
-__device__ __forceinline__ int4 int32_record(int2 ri, int2 rj)
-{
-    const unsigned dx = (unsigned)rj.x - (unsigned)ri.x, dy = (unsigned)rj.y - (unsigned)ri.y;
-    const unsigned c = (unsigned)ri.x * dy - (unsigned)ri.y * dx;
-    return (int)dy > 0 ? make_int4((int)(0u - c), (int)dy, (int)(0u - dx), rj.y)
-                       : make_int4((int)c, (int)(0u - dy), (int)dx, rj.y);
-}
-
-// FP32 record of the edge ri -> rj in the frame with origin (ox, oy) (see PM_BOUND_K).
-__device__ __forceinline__ float4 fp32_record(int2 ri, int2 rj, int ox, int oy)
-{
-    const int dx = rj.x - ri.x, dy = rj.y - ri.y;
-    const float fdx = __int2float_rn(dx), fdy = __int2float_rn(dy);
-    const float X = __int2float_rn(ri.x - ox), Y = __int2float_rn(ri.y - oy);
-    const float c = __fmaf_rn(X, fdy, -__fmul_rn(Y, fdx));
-    return dy > 0 ? make_float4(c, fdy, fdx, __int_as_float(rj.y)) : make_float4(-c, -fdy, -fdx, __int_as_float(rj.y));
-}
 
 template <bool DENSE, bool VERIFY>
 __global__ void __launch_bounds__(WP_THREADS, WP_CTAS) k_pip_warp(ClassifyArgs a, LargeList *ll, int lcap)
@@ -780,6 +656,12 @@ __global__ void __launch_bounds__(LG_THREADS, PPT == 4 ? 3 : 4) k_pip_large(Clas
         s_fail = 0;
     }
     unsigned bar_phase = 0;
+    // A tile wait that gave up leaves the CTA "degraded": the copy may still land in its shared
+    // tile buffer, so from then on the CTA neither issues copies nor touches that buffer and
+    // decides every remaining pair exactly from global memory (same bits, slower); before it
+    // exits it waits, again with a limit, for the copy that was late.
+    bool degraded = false;
+    unsigned fail_phase = 0;
     long long scan_k = blockIdx.x;   // overflow mode: polygons blockIdx.x, + gridDim.x, ...
     const SlabHeader *sh = reinterpret_cast<const SlabHeader *>(a.slab);
     const bool slab_ok = sh && sh->valid && sh->n_polys == P;
@@ -882,6 +764,12 @@ __global__ void __launch_bounds__(LG_THREADS, PPT == 4 ? 3 : 4) k_pip_large(Clas
         __syncthreads();
         for (int e0 = ea; !use_slabs && s_pb[0] <= s_pb[2] && e0 < eb; e0 += T) {
             const int nt = min(T, eb - e0);
+            if (degraded) {   // CTA-uniform: no barrier below is skipped by only some threads
+                #pragma unroll
+                for (int r = 0; r < PPT; ++r)
+                    if (ok[r]) par[r] ^= global_exact_parity(a.verts + base, m, e0, e0 + nt, pt[r]);
+                continue;
+            }
             if (tid == 0) { s_tb[0] = s_pb[0]; s_tb[1] = s_pb[1]; s_tb[2] = s_pb[2]; s_tb[3] = s_pb[3]; }
             // the tile's vertices e0 .. e0 + nt (the last one is vertex 0 when the tile closes the
             // polygon): the 16-byte-aligned interior of the contiguous run by one bulk copy, the
@@ -902,11 +790,17 @@ __global__ void __launch_bounds__(LG_THREADS, PPT == 4 ? 3 : 4) k_pip_large(Clas
                 if (g >= m) g -= m;
                 s_v[i] = __ldg(a.verts + base + g);
             }
-            if (bulk) {
-                if (!mbar_wait(&s_bar, bar_phase, 1 << 22) && !mbar_wait(&s_bar, bar_phase, 1 << 22)) s_fail = 1;
-                bar_phase ^= 1u;
-            }
+            if (bulk && !mbar_wait(&s_bar, bar_phase, 1 << 22) && !mbar_wait(&s_bar, bar_phase, 1 << 22)) s_fail = 1;
             __syncthreads();
+            if (s_fail) {   // read after the barrier, so every thread sees the same value
+                degraded = true;
+                fail_phase = bar_phase;
+                #pragma unroll
+                for (int r = 0; r < PPT; ++r)
+                    if (ok[r]) par[r] ^= global_exact_parity(a.verts + base, m, e0, e0 + nt, pt[r]);
+                continue;
+            }
+            if (bulk) bar_phase ^= 1u;
             int x0 = INT_MAX, y0 = INT_MAX, x1 = INT_MIN, y1 = INT_MIN;
             for (int i = tid; i <= nt; i += LG_THREADS) {
                 const int2 v = s_v[i];
@@ -981,6 +875,8 @@ __global__ void __launch_bounds__(LG_THREADS, PPT == 4 ? 3 : 4) k_pip_large(Clas
         }
         __syncthreads();
     }
+    // a degraded CTA keeps its shared memory until the late copy has landed (bounded wait)
+    if (degraded && tid == 0) mbar_wait(&s_bar, fail_phase, 1 << 22);
     if (a.stats) {
         #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
@@ -994,7 +890,7 @@ __global__ void __launch_bounds__(LG_THREADS, PPT == 4 ? 3 : 4) k_pip_large(Clas
             if (st_fbp) atomicAdd(a.stats + ST_FALLBACK_POINTS, st_fbp);
             if (VERIFY && st_err) atomicAdd(a.stats + ST_FILTER_ERRORS, st_err);
             if (VERIFY && st_ver) atomicAdd(a.stats + ST_VERIFIED, st_ver);
-            if (tid == 0 && s_fail) atomicAdd(a.stats + ST_WAIT_TIMEOUTS, 1ULL);
+            if (tid == 0 && degraded) atomicAdd(a.stats + ST_WAIT_TIMEOUTS, 1ULL);
         }
     }
     // the last CTA to finish empties the list for the next call
@@ -1014,13 +910,19 @@ __global__ void __launch_bounds__(LG_THREADS, PPT == 4 ? 3 : 4) k_pip_large(Clas
 // launch
 // =============================================================================================
 
+// Per-device launch set-up of the kernels (dynamic shared-memory limit, resident CTAs), done on
+// the first launch on each device; calls from several host threads serialise on this lock.
+static std::mutex g_setup_mu;
+
 template <typename K>
 static int ensure_smem(K kernel, size_t smem, size_t *configured)
 {
     int dev = 0;
-    cudaGetDevice(&dev);
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return (int)e;
+    std::lock_guard<std::mutex> lock(g_setup_mu);
     if (dev >= 0 && dev < 64 && configured[dev] < smem) {
-        cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return (int)e;
         configured[dev] = smem;
     }
@@ -1037,14 +939,18 @@ static int launch_warp_d(const ClassifyArgs &a, LargeList *ll, int lcap, int n_s
     if (e) return e;
     int dev = 0;
     cudaGetDevice(&dev);
-    if (dev >= 0 && dev < 64 && blocks_per_sm[dev] == 0) {
-        int nb = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_pip_warp<DENSE, VERIFY>, WP_THREADS, smem) !=
-            cudaSuccess)
-            nb = 1;
-        blocks_per_sm[dev] = std::max(nb, 1);
+    int bps = 1;
+    if (dev >= 0 && dev < 64) {
+        std::lock_guard<std::mutex> lock(g_setup_mu);
+        if (blocks_per_sm[dev] == 0) {
+            int nb = 0;
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_pip_warp<DENSE, VERIFY>, WP_THREADS, smem) !=
+                cudaSuccess)
+                nb = 1;
+            blocks_per_sm[dev] = std::max(nb, 1);
+        }
+        bps = blocks_per_sm[dev];
     }
-    const int bps = (dev >= 0 && dev < 64) ? blocks_per_sm[dev] : 1;
     const long long nchunk = ((long long)a.n_polys + 31) / 32;
     const long long need = (nchunk + WP_THREADS / 32 - 1) / (WP_THREADS / 32);
     const int grid = (int)std::max(1LL, std::min((long long)n_sm * bps, need));
@@ -1076,7 +982,11 @@ static int launch_filtered_v(const ClassifyArgs &a, long long total_bits, const 
         const cudaError_t m = cudaMemsetAsync(a.out_bits, 0, (size_t)a.n_polys * (size_t)a.words_per_poly * 4, stream);
         if (m != cudaSuccess) return (int)m;
     }
-    int e = a.cand_offsets ? launch_warp_d<false, VERIFY>(a, ll, lcap, n_sm, stream)
+    int e;
+    if (t.small_kernel == 1)
+        e = launch_small_cmp(a, ll, lcap, n_sm, t.small_slice, t.small_ctas, VERIFY, stream);
+    else
+        e = a.cand_offsets ? launch_warp_d<false, VERIFY>(a, ll, lcap, n_sm, stream)
                            : launch_warp_d<true, VERIFY>(a, ll, lcap, n_sm, stream);
     if (e) return e;
     const int grid = n_sm * t.ctas_per_sm;

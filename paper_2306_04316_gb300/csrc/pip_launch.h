@@ -10,25 +10,41 @@ namespace pipdev {
 // Counts kernel launches made by the library (host side; pip_launch_count reads it).
 void note_launch(int n = 1);
 
+// Records a CUDA runtime error for pip_last_cuda_error (thread-local) and returns PIP_ERR_CUDA.
+int cuda_fail(cudaError_t e);
+
+// Statistics counters that pip_classify_noalloc keeps in its fixed device array (ST_COUNT values
+// of the current device): added to `h` (reset to 0 when `reset`), nothing when that entry point
+// has not run on this device.  Returns 0 or a CUDA error code.
+int noalloc_stats(unsigned long long *h, bool reset);
+
 struct ClassifyArgs;
 
 struct LargeList;
 
-// Tuned shape of pip_classify's large-polygon kernel.
+// Tuned shapes of pip_classify's kernels.
 struct Tuning {
-    int edge_tile;       // edges staged in shared memory per pass
-    int pts_per_thread;  // candidates carried by each thread (1, 2, 4)
-    int ctas_per_sm;     // resident CTAs per SM
+    int edge_tile;       // large-polygon kernel: edges staged in shared memory per pass
+    int pts_per_thread;  // large-polygon kernel: candidates carried by each thread (1, 2, 4)
+    int ctas_per_sm;     // large-polygon kernel: resident CTAs per SM
     int verify;          // recheck every trusted decision exactly and count disagreements
+    int small_kernel;    // small polygons: 0 = lockstep rounds (k_pip_warp), 1 = compacting (k_pip_cmp)
+    int small_slice;     // compacting kernel: candidates per slice (128, 256)
+    int small_ctas;      // compacting kernel: resident CTAs per SM (0 = as many as fit)
 };
 
 int launch_exact(const ClassifyArgs &a, long long total_bits, int grid, cudaStream_t stream, int rule = 0);
 int launch_filtered(const ClassifyArgs &a, long long total_bits, const Tuning &t, int n_sm, LargeList *ll,
                     int lcap, cudaStream_t stream);
 size_t filtered_smem_bytes(int edge_tile);
+int launch_small_cmp(const ClassifyArgs &a, LargeList *ll, int lcap, int n_sm, int slice, int ctas_per_sm,
+                     bool verify, cudaStream_t stream);
 Tuning current_tuning();   // the values set by pip_set_tuning
 int launch_validate(const ClassifyArgs &a, long long n_verts, long long n_cand_ids, int *d_status, int grid,
                     cudaStream_t stream);
+
+// dst[i] ^= src[i] for i < n (XOR of partial parities)
+int launch_xor_words(uint32_t *dst, const uint32_t *src, long long n, int n_sm, cudaStream_t stream);
 
 // exclusive scan of uint32 in place (multi-level); tmp holds scan_tmp_elems(n) values
 long long scan_tmp_elems(long long n);

@@ -613,3 +613,70 @@ def test_graph_replay_of_binning_and_classification(api):
         got_bits = oracle.unpack_bits(got, n_c)[perm]
         bad = np.nonzero(got_bits != want_bits)[0]
         assert len(bad) == 0, f"graph replay: {len(bad)} of {n_c} bits differ"
+
+
+def _small_kernel_cases():
+    """Workloads that exercise the small-polygon kernels' slicing: one slice per polygon set and
+    several (more candidates than a slice), polygons with no candidates, sets cut by the vertex
+    budget, dense small polygons whose slices span several polygons, int64/FP32 sets, large
+    polygons interleaved with small ones, and invalid ids."""
+    rng = np.random.default_rng(61)
+    cases = [W.footprints(seed=62, n_polys=3000, pts_per_poly=16),
+             W.footprints(seed=63, n_polys=300, pts_per_poly=700),
+             W.footprints(seed=64, n_polys=5000, pts_per_poly=1),
+             W.stress(seed=65, n_polys=4000)]
+    # many polygons without candidates between listed ones
+    polys, csr = [], []
+    for k in range(2000):
+        cx, cy = int(rng.integers(0, 10**6)), int(rng.integers(0, 10**6))
+        m = int(rng.integers(3, 60))
+        ang = np.sort(rng.uniform(0, 2 * np.pi, m))
+        polys.append([(cx + int(300 * np.cos(a)), cy + int(300 * np.sin(a))) for a in ang])
+        csr.append([] if k % 5 else [int(x) for x in rng.integers(0, 4000, int(rng.integers(1, 90)))])
+    pts = rng.integers(0, 10**6, size=(4000, 2))
+    for k in range(0, 2000, 5):
+        for pid in csr[k]:
+            pts[pid] = polys[k][0][0] - int(rng.integers(0, 400)), polys[k][0][1] + int(rng.integers(-200, 200))
+    cases.append(make("sparse-sets", polys, pts, csr))
+    # polygons of 200-256 vertices: every slice holds one polygon
+    polys = [[(int(5000 * k + 2000 * np.cos(a)), int(3000 * np.sin(a)))
+              for a in np.sort(rng.uniform(0, 2 * np.pi, int(rng.integers(200, 257))))] for k in range(60)]
+    pts = [(int(5000 * k + x), int(y)) for k in range(60) for x, y in rng.integers(-2200, 2200, (40, 2))]
+    cases.append(make("vertex-budget", polys, pts, [list(range(40 * k, 40 * k + 40)) for k in range(60)]))
+    # dense: 300 small polygons against 100 points (slices span several polygons' candidates)
+    polys = [[(int(50 * np.cos(a)) + int(rng.integers(-20, 20)), int(50 * np.sin(a)) + int(rng.integers(-20, 20)))
+              for a in np.sort(rng.uniform(0, 2 * np.pi, int(rng.integers(3, 12))))] for _ in range(300)]
+    cases.append(make("dense-small", polys, rng.integers(-60, 60, (100, 2))))
+    # small and large interleaved
+    parts = []
+    for i in range(3):
+        parts.append(W.footprints(seed=66 + i, n_polys=90 + 7 * i, pts_per_poly=5 + 3 * i))
+        parts.append(W.fractal(seed=70 + i, n_polys=1, m_lo=300 + 500 * i, m_hi=301 + 500 * i,
+                               n_points=900 + 77 * i, cell=100_000, grid=1))
+    cases.append(_concat(parts, "interleaved"))
+    return cases
+
+
+@pytest.mark.parametrize("small", [(0, 256, 0), (1, 256, 0), (1, 128, 0), (1, 256, 1), (1, 128, 2)])
+def test_small_kernel_shapes(api, small):
+    """Both small-polygon kernels and every slice size give the oracle's bits."""
+    before = api.pip_get_small_tuning()
+    api.pip_set_small_tuning(*small)
+    try:
+        for w in _small_kernel_cases():
+            want = oracle.classify(w.points, w.poly_offsets, w.verts, w.cand_offsets, w.cand_ids)
+            assert_same(gpu_bits(api, w), want, w.n_bits, f"{w.name} small={small}")
+        # invalid ids are never dereferenced
+        w = W.footprints(seed=75, n_polys=2000, pts_per_poly=16)
+        ids = w.cand_ids.copy()
+        bad = np.random.default_rng(76).choice(len(ids), 300, replace=False)
+        ids[bad[:150]] = -5
+        ids[bad[150:]] = w.n_points + 7
+        got = oracle.unpack_bits(gpu_bits(api, w.with_csr(w.cand_offsets, ids)), w.n_bits)
+        want = oracle.unpack_bits(oracle.classify(w.points, w.poly_offsets, w.verts, w.cand_offsets, w.cand_ids),
+                                  w.n_bits)
+        keep = np.ones(w.n_bits, bool)
+        keep[bad] = False
+        assert not got[bad].any() and np.array_equal(got[keep], want[keep])
+    finally:
+        api.pip_set_small_tuning(*before)

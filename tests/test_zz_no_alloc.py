@@ -4,15 +4,16 @@ Some callers cannot let a library call cudaMalloc (graph capture, their own allo
 fixed memory budget, paths that cannot take its synchronisation).  pip_classify_noalloc keeps
 its scratch -- the list of large polygons -- in a fixed array inside the library instead.
 This file is collected last so that a failure here leaves every other test already run.
-The test calls the entry point through the C ABI and compares its output bit for bit with
-pip_classify's on the same data, on two calls in a row (the array keeps the previous call's
-contents, so the second call checks that it starts clean).
+The test calls the entry point through the C ABI on two calls in a row (the array keeps the
+previous call's contents) and compares each output bit for bit with the CPU oracle and with
+pip_classify's on the same data, in CSR and dense mode.
 """
 import ctypes
 
 import numpy as np
 import pytest
 
+import oracle
 from paper_2306_04316_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
@@ -47,6 +48,7 @@ def test_noalloc_matches_pip_classify_twice():
         pytest.skip("no CUDA device")
     from paper_2306_04316_gb300 import _lib, api, build
     build.build_library()
+    oracle.build()
     lib = _lib.load()
     w = _mixed_workload()
     assert w.n_polys <= _lib.PIP_NOALLOC_MAX_POLYS
@@ -55,6 +57,8 @@ def test_noalloc_matches_pip_classify_twice():
                            n_cands=w.n_bits)
     torch.cuda.synchronize()
     ref = ref.cpu().numpy().view(np.uint32)[:w.n_words]
+    want = oracle.classify(w.points, w.poly_offsets, w.verts, w.cand_offsets, w.cand_ids)
+    assert np.array_equal(ref, want)
     stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
     for call in range(2):
         out = torch.full((w.n_words,), -1, dtype=torch.int32, device="cuda")
@@ -64,17 +68,21 @@ def test_noalloc_matches_pip_classify_twice():
         assert rc == _lib.PIP_OK, lib.pip_status_str(rc)
         torch.cuda.synchronize()
         got = out.cpu().numpy().view(np.uint32)
+        assert np.array_equal(got, want), f"call {call}: {np.count_nonzero(got != want)} words differ from the oracle"
         assert np.array_equal(got, ref), f"call {call}: {np.count_nonzero(got != ref)} words differ"
     # dense mode through the same array
     s = W.star(seed=77, m=1500, n_uniform=3000, n_special=100)
     ds = api.to_device(s)
     ref = api.pip_classify(ds["points"], ds["poly_offsets"], ds["verts"])
-    got = torch.full_like(ref, -1)
-    rc = lib.pip_classify_noalloc(ds["points"].data_ptr(), s.n_points, ds["poly_offsets"].data_ptr(),
-                                  ds["verts"].data_ptr(), s.n_polys, None, None, got.data_ptr(), stream)
-    assert rc == _lib.PIP_OK
-    torch.cuda.synchronize()
-    assert torch.equal(got, ref)
+    want = oracle.classify(s.points, s.poly_offsets, s.verts)
+    for call in range(2):
+        got = torch.full_like(ref, -1)
+        rc = lib.pip_classify_noalloc(ds["points"].data_ptr(), s.n_points, ds["poly_offsets"].data_ptr(),
+                                      ds["verts"].data_ptr(), s.n_polys, None, None, got.data_ptr(), stream)
+        assert rc == _lib.PIP_OK
+        torch.cuda.synchronize()
+        assert np.array_equal(got.cpu().numpy().view(np.uint32), want), f"dense call {call} differs from the oracle"
+        assert torch.equal(got, ref)
     # beyond the limit: rejected before any device work
     rc = lib.pip_classify_noalloc(d["points"].data_ptr(), w.n_points, d["poly_offsets"].data_ptr(),
                                   d["verts"].data_ptr(), _lib.PIP_NOALLOC_MAX_POLYS + 1,
