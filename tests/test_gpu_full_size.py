@@ -1,12 +1,15 @@
 """GPU parity at the full benchmark sizes, through the same calls and default launch
-configuration that bench.py times.
+configuration that bench.py times; every bit is compared with the oracle (0 mismatches).
 
-Footprints (1M polygons, 16M candidates), stress (1M polygons, 8M candidates) and star
-(test_gpu_parity.test_star_full) are compared bit for bit with the oracle, for both kernels.
-The fractal batch (8e11 pair tests) and the spatial join (100k polygons x 10M points) are
-checked on seeded samples that the oracle computes one by one from the generated inputs:
-sampled candidates for the fractal batch; sampled polygons for the join, whose closed-box
-candidate sets and bits the oracle derives by brute force over all 10M points.
+- footprints (1M polygons, 16M candidates), stress (1M polygons, 8M candidates), star
+  (test_gpu_parity.test_star_full), the fractal batch (64 polygons of 1e4-1e6 vertices, 10M
+  points, about 8e11 pair tests) and the paper-shaped country batch (17,097,823 points against
+  one 100,000-vertex polygon, dense): all bits, both kernels;
+- the spatial join (100k polygons against one full 10M-point batch): the GPU candidate lists
+  must equal the closed-box lists computed here from the definition on points sorted by x
+  (that computation is itself checked against the oracle's brute-force join on 100 polygons),
+  and every candidate's bit must equal the oracle's on those lists.
+The sampled tests at the end of the file are quick checks of the same batches.
 """
 import numpy as np
 import pytest
@@ -27,6 +30,59 @@ def test_footprints_full_size(api):
 
 def test_stress_full_size(api):
     check_full(api, W.stress(), "full size")
+
+
+def test_fractal_full_size(api):
+    check_full(api, W.fractal(), "full size")
+
+
+def test_country_full_size(api):
+    check_full(api, W.country(), "full size")
+
+
+def _closed_box_lists(points, poly_offsets, verts):
+    """Candidate lists by the closed-box definition (x0 <= p_x <= x1 and y0 <= p_y <= y1, ids
+    ascending), evaluated on the points sorted by x: a polygon's x-range is a window of that
+    order, whose points are then filtered by y."""
+    po = poly_offsets.astype(np.int64)
+    v = verts.astype(np.int64)
+    m = np.diff(po)
+    starts = np.minimum(po[:-1], max(len(v) - 1, 0))
+    x0, x1 = np.minimum.reduceat(v[:, 0], starts), np.maximum.reduceat(v[:, 0], starts)
+    y0, y1 = np.minimum.reduceat(v[:, 1], starts), np.maximum.reduceat(v[:, 1], starts)
+    order = np.argsort(points[:, 0], kind="stable")
+    xs, ys = points[order, 0], points[order, 1]
+    lo, hi = np.searchsorted(xs, x0, "left"), np.searchsorted(xs, x1, "right")
+    lists = []
+    for k in range(len(m)):
+        if m[k] == 0:
+            lists.append(np.zeros(0, dtype=np.int64))
+            continue
+        yy = ys[lo[k]:hi[k]]
+        lists.append(np.sort(order[lo[k]:hi[k]][(yy >= y0[k]) & (yy <= y1[k])]))
+    co = np.zeros(len(m) + 1, dtype=np.int64)
+    co[1:] = np.cumsum([len(t) for t in lists])
+    return co, np.concatenate(lists).astype(np.int64)
+
+
+def test_join_full_batch(api):
+    """One full join batch: 100k polygons, 10M clustered points, binned and classified on the GPU."""
+    w = W.join()
+    want_co, want_ids = _closed_box_lists(w.points, w.poly_offsets, w.verts)
+    # the window computation against the oracle's brute-force join, on 100 polygons
+    polys = np.sort(np.random.default_rng(2306043160 + 80).choice(w.n_polys, 100, replace=False))
+    counts, ids_o = oracle.bbox_join(w.points, w.poly_offsets, w.verts, polys)
+    assert np.array_equal(counts, want_co[polys + 1] - want_co[polys])
+    assert np.array_equal(ids_o, np.concatenate([want_ids[want_co[k]:want_co[k + 1]] for k in polys]))
+    d = api.to_device(w)
+    co, ids = api.bin_join(d["points"], d["poly_offsets"], d["verts"])
+    n_c = int(co[-1].item())
+    out = api.pip_classify(d["points"], d["poly_offsets"], d["verts"], co, ids, n_cands=n_c)
+    torch.cuda.synchronize()
+    assert np.array_equal(co.cpu().numpy().astype(np.int64), want_co), "candidate offsets"
+    assert np.array_equal(ids.cpu().numpy()[:n_c].astype(np.int64), want_ids), "candidate ids"
+    want = oracle.classify(w.points, w.poly_offsets, w.verts, want_co, want_ids)
+    assert_same(out.cpu().numpy().view(np.uint32)[:len(want)], want, n_c, "join full batch")
 
 
 def test_fractal_full_size_sampled(api):
