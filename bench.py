@@ -314,16 +314,18 @@ def arithmetic_of(w):
     return "+".join(kinds)
 
 
-def run_join(args, rank, world):
+def run_join(args, rank, world, quiet=False):
     """Spatial join: 100k footprint polygons against 20 batches of 10M clustered points; one
-    step = one replay of a CUDA graph that bins and classifies all 20 batches."""
+    step = one replay of a CUDA graph that bins and classifies all 20 batches.  With ``quiet``
+    (a compact measurement for another workload's line) the line is returned, not printed, and
+    the end-to-end leg, the CPU baseline and the clock sampler are skipped."""
     import numpy as np
     import torch
     from paper_2306_04316_gb300 import api, build as pbuild, workloads as W
 
     pbuild.build_library()
     torch.cuda.set_device(_env_int("LOCAL_RANK", 0))
-    dist = dist_setup(world)
+    dist = None if quiet else dist_setup(world)
     nb = args.batches
     n_pts = int(10_000_000 * args.scale)
     seed = W.BASE_SEED + 3 + 1000 * rank
@@ -356,7 +358,8 @@ def run_join(args, rank, world):
 
     # pinned host buffers of the end-to-end step: the batches' points in, their bits and candidate
     # CSR out
-    if not args.no_e2e:
+    with_e2e = not args.no_e2e and not quiet
+    if with_e2e:
         h_pts = [torch.from_numpy(x).pin_memory() for x in host_pts]
         h_out = [torch.empty(o.numel(), dtype=torch.int32).pin_memory() for o in outs]
         h_ids = [torch.empty(t_, dtype=torch.int32).pin_memory() for t_ in totals]
@@ -404,7 +407,7 @@ def run_join(args, rank, world):
         per_replay[name] = api.pip_launch_count() - l0
         graphs[name] = g
     g_e2e = None
-    if not args.no_e2e:
+    if with_e2e:
         g_e2e = torch.cuda.CUDAGraph()
         with torch.cuda.graph(g_e2e, stream=stream):
             one_pass(True, io=True)
@@ -415,7 +418,7 @@ def run_join(args, rank, world):
                 g.replay()
         stream.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        sampler = ClockSampler(_env_int("LOCAL_RANK", 0)) if name == "full" else None
+        sampler = ClockSampler(_env_int("LOCAL_RANK", 0)) if name == "full" and not quiet else None
         if sampler:
             sampler.start()
         if dist:
@@ -470,7 +473,7 @@ def run_join(args, rank, world):
     peaks, peak_kind = measured_peaks()
     hbm = float(peaks["hbm_gbs"])
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and not quiet:
         sub_p = min(P, 2000)
         sub = W.Workload("join-sample", host_pts[0][:1_000_000], po[:sub_p + 1], v[:int(po[sub_p])])
         co_s, ids_s = W.bbox_csr(sub.poly_offsets.astype(np.int64), sub.verts, sub.points)
@@ -494,10 +497,182 @@ def run_join(args, rank, world):
                              "peak_source": peak_kind, "kernel": "binning + k_pip_warp + k_pip_large (whole step)",
                              "algorithmic_bytes": join_bytes, "kernel_ms": ms},
                 "e2e": e2e}
+        if quiet:
+            return line
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
     return 0
+
+
+def run_strong(args, rank, world):
+    """One global batch split across the ranks (strong scaling): the footprint and stress
+    batches by contiguous polygon ranges balanced by pair tests, each rank writing its bits at
+    their global positions of a zeroed full-size output, combined by an integer SUM all-reduce
+    (the ranks' bits are disjoint); the fractal and country batches by edge pieces closed
+    through each polygon's first vertex, combined by all-gather and XOR.  A step is the memset,
+    the rank's pip_classify call and the combine; the time is the slowest rank's."""
+    import numpy as np
+    import torch
+    from paper_2306_04316_gb300 import api, build as pbuild, shard
+
+    pbuild.build_library()
+    local = _env_int("LOCAL_RANK", 0)
+    torch.cuda.set_device(local)
+    dist = dist_setup(world)
+    w = make_workload(args.workload, 0, args.scale)   # the same global batch on every rank
+    T, C = w.pair_tests(), w.n_candidates
+    by_edges = w.dense or args.workload in ("fractal", "country")
+    pts = torch.from_numpy(w.points).cuda()
+    if by_edges:
+        ppo, pv = shard.edge_pieces(w.poly_offsets, w.verts, world)[rank]
+        po, v = torch.from_numpy(ppo).cuda(), torch.from_numpy(pv).cuda()
+        co = None if w.dense else torch.from_numpy(w.cand_offsets).cuda()
+        ids = None if w.dense else torch.from_numpy(w.cand_ids).cuda()
+        part = f"edge pieces closed through R_0, {world} per polygon"
+    else:
+        b = shard.polygon_ranges(w.poly_offsets, w.cand_offsets, world)
+        p0, p1 = int(b[rank]), int(b[rank + 1])
+        po = torch.from_numpy(w.poly_offsets[p0:p1 + 1]).cuda()
+        v = torch.from_numpy(w.verts).cuda()
+        co = torch.from_numpy(w.cand_offsets[p0:p1 + 1]).cuda()
+        ids = torch.from_numpy(w.cand_ids).cuda()
+        part = "contiguous polygon ranges balanced by pair tests"
+    out = torch.zeros(max(w.n_words, 1), dtype=torch.int32, device="cuda")
+    stream = torch.cuda.Stream()
+    n_bits = None if w.dense else w.n_bits
+
+    def step():
+        out.zero_()
+        if int(po.shape[0]) > 1:
+            api.pip_classify(pts, po, v, co, ids, out=out, n_cands=n_bits)
+        if by_edges:
+            shard.combine_xor(out, dist)
+        else:
+            shard.combine_disjoint(out, dist)
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            step()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        e0.record(stream)
+        for _ in range(args.steps):
+            step()
+        e1.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    ms = max_over_ranks(dist, e0.elapsed_time(e1) / args.steps)
+    if rank == 0:
+        line = {"metric": METRIC, "value": job_rate(T, ms), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "strong",
+                "vs_baseline": None, "dtype": arithmetic_of(w), "data": "synthetic",
+                "config": {"workload": f"{w.name}: {w.n_polys} polygons, {C} candidates (one global batch)",
+                           "partition": part, "pair_tests_per_step": T,
+                           "timing": "memset + pip_classify + combine per step, direct calls"},
+                "points_per_s": job_rate(C, ms), "gpu_launches": None}
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def roofline_of(T, B, kern_ms, peaks, peak_kind, n_sm, kernel, traffic=None):
+    """Roofline of a classify step: t_roof = max(T / P_pair, B / BW), P_pair = N_SM x 128 lanes x
+    f_max / 4 lane-instructions per pair, BW = the measured HBM copy bandwidth; the bound is
+    whichever term is larger, and frac = achieved / peak for that term."""
+    f_max = float(peaks.get("sm_max_mhz", 2070.0)) * 1e6
+    pair_peak = n_sm * 128 * f_max / 4.0
+    hbm = float(peaks["hbm_gbs"])
+    if B / (hbm * 1e9) >= T / pair_peak:
+        achieved = B / (kern_ms / 1000.0) / 1e9
+        return {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                "traffic": traffic, "peak_source": peak_kind, "kernel": kernel, "algorithmic_bytes": B,
+                "kernel_ms": kern_ms}
+    achieved = T / (kern_ms / 1000.0)
+    return {"bound": "alu", "achieved": achieved / 1e12, "peak": pair_peak / 1e12, "unit": "Tpair/s",
+            "frac": achieved / pair_peak, "traffic": traffic,
+            "peak_source": f"{n_sm} SMs x 128 lanes x {f_max / 1e6:.0f} MHz / 4 lane-instructions per pair",
+            "kernel": kernel, "algorithmic_bytes": B, "kernel_ms": kern_ms}
+
+
+def time_graph_steps(call, stream, steps, warmup, flush_bytes=0):
+    """Mean CUDA-event time (ms) of one replay of a graph holding ``call``, timed on ``stream``
+    after warm-up; with flush_bytes, that many bytes are written between steps, outside the
+    timed intervals (an L2 flush)."""
+    import statistics as st_
+    import torch
+    with torch.cuda.stream(stream):
+        for _ in range(2):
+            call()
+    stream.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=stream):
+        call()
+    flush = torch.empty(flush_bytes, dtype=torch.uint8, device="cuda") if flush_bytes else None
+    with torch.cuda.stream(stream):
+        for _ in range(warmup):
+            g.replay()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    with torch.cuda.stream(stream):
+        for e0, e1 in ev:
+            if flush is not None:
+                flush.zero_()
+            e0.record(stream)
+            g.replay()
+            e1.record(stream)
+    torch.cuda.synchronize()
+    return st_.mean(e0.elapsed_time(e1) for e0, e1 in ev)
+
+
+def other_configs(args, peaks, peak_kind, n_sm):
+    """Compact device-timed measurements of the other workloads at their full sizes (one GPU, no
+    CPU baseline): star, stress, fractal, country with pip_classify, the join with its whole
+    binning + classification step."""
+    import gc
+    import torch
+    from paper_2306_04316_gb300 import api
+    res = {}
+    stream = torch.cuda.Stream()
+    for name, steps in (("star", 20), ("stress", 20), ("fractal", 4), ("country", 3)):
+        w = make_workload(name, 0, 1.0)
+        T, B = w.pair_tests(), w.algorithmic_bytes()
+        d = api.to_device(w)
+        out = torch.empty(w.n_words, dtype=torch.int32, device="cuda")
+        co, ci = d.get("cand_offsets"), d.get("cand_ids")
+
+        def call():
+            api.pip_classify(d["points"], d["poly_offsets"], d["verts"], co, ci, out=out)
+        api.pip_reset_stats()
+        ms = time_graph_steps(call, stream, steps, 3, 256 * 2**20 if B < 160 * 10**6 else 0)
+        stt = api.pip_get_stats()
+        roof = roofline_of(T, B, ms, peaks, peak_kind, n_sm, "pip_classify")
+        res[name] = {"workload": f"{w.name}: {w.n_polys} polygons, {w.n_candidates} candidates, "
+                                 f"{w.verts.shape[0]} vertices", "steps": steps, "ms_per_step": ms,
+                     "pair_tests_per_s": T / (ms / 1000.0), "points_per_s": w.n_candidates / (ms / 1000.0),
+                     "roofline": {k: roof[k] for k in ("bound", "achieved", "peak", "unit", "frac")},
+                     "dtype": arithmetic_of(w),
+                     "fallback_fraction": stt["fallback_points"] / stt["candidates"] if stt["candidates"] else None,
+                     "wait_timeouts": stt["wait_timeouts"]}
+        del d, out, w
+        gc.collect()
+        torch.cuda.empty_cache()
+    jargs = argparse.Namespace(**vars(args))
+    jargs.steps, jargs.warmup, jargs.scale = 3, 3, 1.0
+    jl = run_join(jargs, 0, 1, quiet=True)
+    res["join"] = {"workload": jl["config"]["workload"], "steps": 3, "ms_per_step": jl["ms_per_step"],
+                   "pair_tests_per_s": jl["value"], "points_per_s": jl["points_per_s"],
+                   "binning_ms_per_step": jl["config"]["binning_ms_per_step"],
+                   "roofline": {k: jl["roofline"][k] for k in ("bound", "achieved", "peak", "unit", "frac")},
+                   "dtype": jl["dtype"]}
+    gc.collect()
+    torch.cuda.empty_cache()
+    return res
 
 
 def main():
@@ -522,6 +697,11 @@ def main():
     ap.add_argument("--scale", type=float, default=1.0, help="fraction of the full batch (tests only)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--scaling", default="weak", choices=["weak", "strong"],
+                    help="weak: every rank classifies its own batch; strong: one global batch split across "
+                         "the ranks (polygon ranges, or edge pieces for the large polygons) and combined")
+    ap.add_argument("--no-other-configs", action="store_true",
+                    help="skip the compact measurements of the other workloads on the footprint line")
     ap.add_argument("--no-graph", action="store_true",
                     help="time direct calls instead of replays of a CUDA graph holding one call")
     ap.add_argument("--e2e-steps", type=int, default=20)
@@ -529,6 +709,9 @@ def main():
     ap.add_argument("--streams", type=int, default=4,
                     help="join workload: streams the batches are spread over inside the graph")
     ap.add_argument("--tuning", default="", help="edge_tile,pts_per_thread,ctas_per_sm (0 = keep)")
+    ap.add_argument("--small-tuning", default="",
+                    help="small-polygon kernel: kernel,slice,ctas_per_sm (kernel 1 = compacting, 0 = lockstep; "
+                         "-1 / 0 keep a value)")
     ap.add_argument("--autotune", action="store_true",
                     help="pick the large-polygon kernel's tuning with the autotuner before timing "
                          "(always on for --workload join)")
@@ -542,6 +725,8 @@ def main():
         return run_reference(args, rank, world)
     if args.workload == "join":
         return run_join(args, rank, world)
+    if args.scaling == "strong":
+        return run_strong(args, rank, world)
 
     import numpy as np
     import torch
@@ -551,6 +736,8 @@ def main():
     torch.cuda.set_device(local)
     if args.tuning:
         api.pip_set_tuning(*[int(x) for x in args.tuning.split(",")])
+    if args.small_tuning:
+        api.pip_set_small_tuning(*[int(x) for x in args.small_tuning.split(",")])
     dist = dist_setup(world)
 
     w = make_workload(args.workload, rank, args.scale)
@@ -703,25 +890,16 @@ def main():
     peaks, peak_kind = measured_peaks()
     props = torch.cuda.get_device_properties(local)
     n_sm = props.multi_processor_count
-    f_max = float(peaks.get("sm_max_mhz", 2070.0)) * 1e6
-    pair_peak = n_sm * 128 * f_max / 4.0
-    t_hbm = B / (float(peaks["hbm_gbs"]) * 1e9)
-    t_alu = T / pair_peak
-    bound = "hbm" if t_hbm >= t_alu else "alu"
     achieved_gbs = B / (kern_ms / 1000.0) / 1e9
-    achieved_pairs = T / (kern_ms / 1000.0)
     traffic = profiled_traffic(args.workload) if args.kernel == "filtered" and args.scale == 1.0 else None
-    if bound == "hbm":
-        roof = {"bound": "hbm", "achieved": achieved_gbs, "peak": float(peaks["hbm_gbs"]), "unit": "GB/s",
-                "frac": achieved_gbs / float(peaks["hbm_gbs"]), "traffic": traffic,
-                "peak_source": peak_kind, "kernel": "k_pip_warp + k_pip_large" if args.kernel == "filtered" else "k_pip_exact",
-                "algorithmic_bytes": B, "kernel_ms": kern_ms}
-    else:
-        roof = {"bound": "alu", "achieved": achieved_pairs / 1e12, "peak": pair_peak / 1e12,
-                "unit": "Tpair/s", "frac": achieved_pairs / pair_peak, "traffic": traffic,
-                "peak_source": f"{n_sm} SMs x 128 lanes x {f_max / 1e6:.0f} MHz / 4 lane-instructions per pair",
-                "kernel": "k_pip_warp + k_pip_large" if args.kernel == "filtered" else "k_pip_exact",
-                "algorithmic_bytes": B, "kernel_ms": kern_ms}
+    small_name = "k_pip_cmp" if api.pip_get_small_tuning()[0] == 1 else "k_pip_warp"
+    roof = roofline_of(T, B, kern_ms, peaks, peak_kind, n_sm,
+                       f"{small_name} + k_pip_large" if args.kernel == "filtered" else "k_pip_exact", traffic)
+    other_roof = None
+    if other_ms:
+        other_roof = roofline_of(T, B, other_ms, peaks, peak_kind, n_sm,
+                                 "k_pip_exact" if args.kernel == "filtered" else f"{small_name} + k_pip_large")
+        other_roof = {k: other_roof[k] for k in ("bound", "achieved", "peak", "unit", "frac", "kernel")}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -747,8 +925,14 @@ def main():
         semantics = {"rule": args.semantics, "bits_differing_from_half_open": diff,
                      "fraction_of_candidates": diff / max(1, w.n_candidates)}
 
+    others = None
     if rank == 0:
         stats = api.pip_get_stats()
+        if (world == 1 and args.workload == "footprints" and args.scale == 1.0 and not args.no_other_configs
+                and args.kernel == "filtered" and args.semantics == "halfopen" and args.index == "none"):
+            del d, out
+            torch.cuda.empty_cache()
+            others = other_configs(args, peaks, peak_kind, n_sm)
         line = {
             "metric": METRIC, "value": job_rate(T_all, ms_step), "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
@@ -758,7 +942,8 @@ def main():
             "config": {"workload": f"{w.name}: {w.n_polys} polygons, {w.n_candidates} candidates, "
                                    f"{w.verts.shape[0]} vertices", "pair_tests_per_step": T,
                        "algorithmic_bytes_per_step": B, "kernel": args.kernel,
-                       "tuning": list(api.pip_get_tuning()), "autotuned": autotuned,
+                       "tuning": list(api.pip_get_tuning()), "small_tuning": list(api.pip_get_small_tuning()),
+                       "autotuned": autotuned,
                        "timing": "one CUDA-graph replay per step" if graph is not None else "direct calls",
                        "l2": ("L2 flushed between steps (256 MB write, outside the timed intervals)"
                               if flush is not None else "inputs larger than L2 (no flush)")},
@@ -770,9 +955,13 @@ def main():
             "clocks": clocks,
             "other_kernel": {"kernel": "exact" if args.kernel == "filtered" else "filtered",
                              "ms_per_step": other_ms,
-                             "value": (T / (other_ms / 1000.0)) if other_ms else None},
+                             "value": (T / (other_ms / 1000.0)) if other_ms else None,
+                             "roofline": other_roof},
             "fallback_fraction": (stats["fallback_points"] / stats["candidates"]) if stats["candidates"] else None,
+            "wait_timeouts": stats["wait_timeouts"],
         }
+        if others is not None:
+            line["other_configs"] = others
         if verification is not None:
             line["verification"] = verification
         if index_info:
