@@ -200,7 +200,8 @@ def _threaded_sample(w, sample, threads):
                                                       w.cand_ids), parts))
 
 
-KERNEL_SOURCES = ["paper_2306_04316_gb300/csrc/pip_filtered.cu", "paper_2306_04316_gb300/csrc/pip_device.cuh",
+KERNEL_SOURCES = ["paper_2306_04316_gb300/csrc/pip_filtered.cu", "paper_2306_04316_gb300/csrc/pip_small.cu",
+                  "paper_2306_04316_gb300/csrc/pip_edge.cuh", "paper_2306_04316_gb300/csrc/pip_device.cuh",
                   "paper_2306_04316_gb300/csrc/pip_launch.h"]
 
 
@@ -213,10 +214,10 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(workload):
+def profiled_traffic(workload, kernel="k_pip_warp"):
     """DRAM bytes per launch of the classify kernel from the committed ncu summary, or None when
     the kernel sources changed since that capture (or no summary covers this workload)."""
-    path = os.path.join(ROOT, "profiles", f"k_pip_warp_{workload}.md")
+    path = os.path.join(ROOT, "profiles", f"{kernel}_{workload}.md")
     if not os.path.exists(path):
         return None
     vals = {}
@@ -713,8 +714,10 @@ def main():
                     help="small-polygon kernel: kernel,slice,ctas_per_sm (kernel 1 = compacting, 0 = lockstep; "
                          "-1 / 0 keep a value)")
     ap.add_argument("--autotune", action="store_true",
-                    help="pick the large-polygon kernel's tuning with the autotuner before timing "
+                    help="also pick the large-polygon kernel's tuning with the autotuner before timing "
                          "(always on for --workload join)")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="keep the library's small-polygon kernel shape instead of tuning it on the batch")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -747,11 +750,21 @@ def main():
     n_words = w.n_words
     out = torch.empty(n_words, dtype=torch.int32, device="cuda")
     autotuned = None
-    if args.autotune and args.kernel == "filtered":
+    if args.kernel == "filtered" and args.semantics == "halfopen":
         from paper_2306_04316_gb300 import tuning
-        best, times = tuning.autotune(d["points"], d["poly_offsets"], d["verts"], d.get("cand_offsets"),
-                                      d.get("cand_ids"), n_cands=None if w.dense else w.n_bits, cache=False)
-        autotuned = {"best": list(best), "candidates": len(times), "best_ms": times[best]}
+        n_c = None if w.dense else w.n_bits
+        autotuned = {}
+        if not args.small_tuning and not args.no_autotune:
+            # the small-polygon kernel's shape, picked on this batch (a few ms of timed calls)
+            best, times = tuning.autotune_small(d["points"], d["poly_offsets"], d["verts"], d.get("cand_offsets"),
+                                                d.get("cand_ids"), n_cands=n_c, cache=False)
+            autotuned["small"] = {"best": list(best), "candidates": len(times), "best_ms": times[best],
+                                  "ms": {",".join(map(str, k)): v for k, v in times.items()}}
+        if args.autotune:
+            best, times = tuning.autotune(d["points"], d["poly_offsets"], d["verts"], d.get("cand_offsets"),
+                                          d.get("cand_ids"), n_cands=n_c, cache=False)
+            autotuned["large"] = {"best": list(best), "candidates": len(times), "best_ms": times[best]}
+        autotuned = autotuned or None
     fn = api.pip_classify if args.kernel == "filtered" else api.pip_classify_exact
     if args.semantics != "halfopen":
         algorithm = 1 if args.semantics == "alg1" else 2
@@ -891,8 +904,8 @@ def main():
     props = torch.cuda.get_device_properties(local)
     n_sm = props.multi_processor_count
     achieved_gbs = B / (kern_ms / 1000.0) / 1e9
-    traffic = profiled_traffic(args.workload) if args.kernel == "filtered" and args.scale == 1.0 else None
     small_name = "k_pip_cmp" if api.pip_get_small_tuning()[0] == 1 else "k_pip_warp"
+    traffic = profiled_traffic(args.workload, small_name) if args.kernel == "filtered" and args.scale == 1.0 else None
     roof = roofline_of(T, B, kern_ms, peaks, peak_kind, n_sm,
                        f"{small_name} + k_pip_large" if args.kernel == "filtered" else "k_pip_exact", traffic)
     other_roof = None

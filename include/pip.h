@@ -287,9 +287,9 @@ int pip_get_tuning(int32_t *edge_tile, int32_t *pts_per_thread, int32_t *ctas_pe
  *                rounds of 32 consecutive candidates; 1 = compacting kernel: the candidates of a
  *                slice that lie inside their polygon's box are packed together before the edge
  *                walk, and each slice's loads are issued one slice ahead; -1 keeps the value
- *   slice        compacting kernel: candidates per slice, 128 or 256 (default); 0 keeps it
- *   ctas_per_sm  compacting kernel: resident CTAs per SM, 1..16, 0 = as many as fit (default);
- *                -1 keeps it
+ *   slice        candidates per slice (both kernels), 128 or 256 (default); 0 keeps it
+ *   ctas_per_sm  resident CTAs per SM of either kernel's persistent grid, 1..16, 0 = as many as
+ *                fit (default); -1 keeps it
  * Applies to later calls on every device; PIP_ERR_INVALID for an out-of-range value.
  */
 int pip_set_small_tuning(int32_t kernel, int32_t slice, int32_t ctas_per_sm);

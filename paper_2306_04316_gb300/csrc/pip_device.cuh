@@ -77,6 +77,13 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned pari
     return false;
 }
 
+// Programmatic dependent launch: a kernel launched with programmatic stream serialization may
+// start while the kernel before it on the stream is still running; pdl_wait blocks until that
+// kernel has completed and its memory operations are visible (a no-op without the attribute),
+// and pdl_trigger lets the next kernel start launching early.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;\n" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory"); }
+
 // 8- and 4-byte asynchronous global -> shared copies (LDGSTS) and their group fences.
 __device__ __forceinline__ void cp_async8(void *smem_dst, const void *gmem_src)
 {

@@ -86,9 +86,9 @@ constexpr int LG_THREADS = 256;
 
 constexpr int WP_THREADS = 128;     // 4 independent warps per CTA
 constexpr int WP_CTAS = 5;          // CTAs per SM (shared memory: 4 x 9.8 KB per CTA)
-constexpr int WP_R = 8;             // candidate rounds of 32 per slice
-constexpr int WP_C = 32 * WP_R;     // candidates of a slice
 
+// WP_R: candidate rounds of 32 per slice (4 or 8; a tuning choice), WP_C = 32 WP_R candidates
+template <int WP_R, int WP_C = 32 * WP_R>
 struct __align__(16) WarpSmem {
     float4 rec[WP_V];               // edge records of the run (int32, int64 or FP32, per polygon)
     int2 v[WP_V];                   // the run's vertices
@@ -100,12 +100,14 @@ struct __align__(16) WarpSmem {
     unsigned char vp[WP_V];         // vertex -> chunk polygon
 };
 
-template <bool DENSE, bool VERIFY>
+template <bool DENSE, bool VERIFY, int WP_R>
 __global__ void __launch_bounds__(WP_THREADS, WP_CTAS) k_pip_warp(ClassifyArgs a, LargeList *ll, int lcap)
 {
     using CI = typename std::conditional<DENSE, long long, int>::type;
     extern __shared__ __align__(16) unsigned char dsm[];
-    WarpSmem &S = reinterpret_cast<WarpSmem *>(dsm)[threadIdx.x >> 5];
+    constexpr int WP_C = 32 * WP_R;     // candidates of a slice
+    WarpSmem<WP_R> &S = reinterpret_cast<WarpSmem<WP_R> *>(dsm)[threadIdx.x >> 5];
+    pdl_trigger();   // the large-polygon kernel may launch now; it waits for this grid to finish
     const unsigned rec_base = (unsigned)__cvta_generic_to_shared(S.rec);
     const int lane = threadIdx.x & 31;
     const unsigned lemask = 0xffffffffu >> (31 - lane);   // lanes 0..lane
@@ -648,6 +650,7 @@ __global__ void __launch_bounds__(LG_THREADS, PPT == 4 ? 3 : 4) k_pip_large(Clas
     const int P = a.n_polys;
     const long long W32 = a.words_per_poly * 32;
     unsigned long long st_cand = 0, st_fbp = 0, st_err = 0, st_ver = 0;
+    pdl_wait();   // the small-polygon kernel before it on the stream has filled the list
     const int count = *((volatile int *)&ll->count);
     const bool scan = *((volatile int *)&ll->overflow) != 0;
     if (count == 0 && !scan) return;   // nothing listed: the header is already clear for the next call
@@ -929,13 +932,14 @@ static int ensure_smem(K kernel, size_t smem, size_t *configured)
     return 0;
 }
 
-template <bool DENSE, bool VERIFY>
-static int launch_warp_d(const ClassifyArgs &a, LargeList *ll, int lcap, int n_sm, cudaStream_t stream)
+template <bool DENSE, bool VERIFY, int R>
+static int launch_warp_r(const ClassifyArgs &a, LargeList *ll, int lcap, int n_sm, int ctas_per_sm,
+                         cudaStream_t stream)
 {
     static size_t configured[64] = {0};
     static int blocks_per_sm[64] = {0};
-    const size_t smem = sizeof(WarpSmem) * (WP_THREADS / 32);
-    int e = ensure_smem(k_pip_warp<DENSE, VERIFY>, smem, configured);
+    const size_t smem = sizeof(WarpSmem<R>) * (WP_THREADS / 32);
+    int e = ensure_smem(k_pip_warp<DENSE, VERIFY, R>, smem, configured);
     if (e) return e;
     int dev = 0;
     cudaGetDevice(&dev);
@@ -944,19 +948,28 @@ static int launch_warp_d(const ClassifyArgs &a, LargeList *ll, int lcap, int n_s
         std::lock_guard<std::mutex> lock(g_setup_mu);
         if (blocks_per_sm[dev] == 0) {
             int nb = 0;
-            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_pip_warp<DENSE, VERIFY>, WP_THREADS, smem) !=
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_pip_warp<DENSE, VERIFY, R>, WP_THREADS, smem) !=
                 cudaSuccess)
                 nb = 1;
             blocks_per_sm[dev] = std::max(nb, 1);
         }
         bps = blocks_per_sm[dev];
     }
+    if (ctas_per_sm > 0) bps = std::min(bps, ctas_per_sm);
     const long long nchunk = ((long long)a.n_polys + 31) / 32;
     const long long need = (nchunk + WP_THREADS / 32 - 1) / (WP_THREADS / 32);
     const int grid = (int)std::max(1LL, std::min((long long)n_sm * bps, need));
-    k_pip_warp<DENSE, VERIFY><<<grid, WP_THREADS, smem, stream>>>(a, ll, lcap);
+    k_pip_warp<DENSE, VERIFY, R><<<grid, WP_THREADS, smem, stream>>>(a, ll, lcap);
     note_launch();
     return (int)cudaGetLastError();
+}
+
+template <bool DENSE, bool VERIFY>
+static int launch_warp_d(const ClassifyArgs &a, LargeList *ll, int lcap, int n_sm, int slice, int ctas_per_sm,
+                         cudaStream_t stream)
+{
+    return slice == 128 ? launch_warp_r<DENSE, VERIFY, 4>(a, ll, lcap, n_sm, ctas_per_sm, stream)
+                        : launch_warp_r<DENSE, VERIFY, 8>(a, ll, lcap, n_sm, ctas_per_sm, stream);
 }
 
 template <int PPT, bool VERIFY>
@@ -967,9 +980,21 @@ static int launch_large_ppt(const ClassifyArgs &a, long long total_bits, LargeLi
     const size_t smem = filtered_smem_bytes(T);
     int e = ensure_smem(k_pip_large<PPT, VERIFY>, smem, configured);
     if (e) return e;
-    k_pip_large<PPT, VERIFY><<<grid, LG_THREADS, smem, stream>>>(a, total_bits, ll, lcap, T);
+    // launched with programmatic stream serialization: its launch overlaps the end of the
+    // small-polygon kernel, and pdl_wait at its start waits for that kernel's completion
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(LG_THREADS);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    const cudaError_t le = cudaLaunchKernelEx(&cfg, k_pip_large<PPT, VERIFY>, a, total_bits, ll, lcap, T);
     note_launch();
-    return (int)cudaGetLastError();
+    return le != cudaSuccess ? (int)le : (int)cudaGetLastError();
 }
 
 template <bool VERIFY>
@@ -986,8 +1011,8 @@ static int launch_filtered_v(const ClassifyArgs &a, long long total_bits, const 
     if (t.small_kernel == 1)
         e = launch_small_cmp(a, ll, lcap, n_sm, t.small_slice, t.small_ctas, VERIFY, stream);
     else
-        e = a.cand_offsets ? launch_warp_d<false, VERIFY>(a, ll, lcap, n_sm, stream)
-                           : launch_warp_d<true, VERIFY>(a, ll, lcap, n_sm, stream);
+        e = a.cand_offsets ? launch_warp_d<false, VERIFY>(a, ll, lcap, n_sm, t.small_slice, t.small_ctas, stream)
+                           : launch_warp_d<true, VERIFY>(a, ll, lcap, n_sm, t.small_slice, t.small_ctas, stream);
     if (e) return e;
     const int grid = n_sm * t.ctas_per_sm;
     switch (t.pts_per_thread) {

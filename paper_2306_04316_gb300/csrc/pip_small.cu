@@ -24,8 +24,8 @@
 //      polygon, so only in-box candidates are walked (on building footprints with points
 //      uniform in a 1.5x box, 44 % of them);
 //   4. the next slice's points are gathered into the other point buffer (cp.async);
-//   5. pass 2, a lane per compacted candidate: the lanes walk their polygons' edge records in
-//      lockstep, a lane whose polygon is shorter repeating its last record (a repeated edge never
+//   5. pass 2, a lane per compacted candidate (two per lane in int32 sets): the lanes walk their
+//      polygons' edge records in lockstep, a lane whose polygon is shorter repeating its last record (a repeated edge never
 //      straddles, so it adds nothing), and store their parities as per-slot bytes;
 //   6. ballots of the per-slot bytes give the slice's output words; the first and last word may
 //      be shared with a neighbouring slice or polygon and take a masked AND/OR pair.
@@ -118,6 +118,7 @@ __global__ void __launch_bounds__(SC_THREADS, 4) k_pip_cmp(ClassifyArgs a, Large
     constexpr int NR = CS / 32;                       // slot rounds of a slice
     extern __shared__ __align__(16) unsigned char dsm[];
     CmpSmem<CS> &S = reinterpret_cast<CmpSmem<CS> *>(dsm)[threadIdx.x >> 5];
+    pdl_trigger();   // the large-polygon kernel may launch now; it waits for this grid to finish
     const unsigned rec_base = (unsigned)__cvta_generic_to_shared(S.rec);
     const int lane = threadIdx.x & 31;
     const unsigned lemask = 0xffffffffu >> (31 - lane);   // lanes 0..lane
@@ -425,8 +426,59 @@ __global__ void __launch_bounds__(SC_THREADS, 4) k_pip_cmp(ClassifyArgs a, Large
         unsigned validm_n = 0;
         if (Dn.ch >= 0) validm_n = gather(Dn, S.pt[cur ^ 1]);
 
-        // ---- pass 2: the compacted candidates walk their polygons' records in lockstep
-        for (int r0 = 0; r0 < ncomp; r0 += 32) {
+        // ---- pass 2: the compacted candidates walk their polygons' records in lockstep.  Int32
+        //      sets: each lane takes two candidates (positions r0 + lane and r0 + 32 + lane), two
+        //      independent chains over one loop, so a round covers 64 candidates
+        if (set_all32) {
+            for (int r0 = 0; r0 < ncomp; r0 += 64) {
+                const int pa = r0 + lane, pb2 = r0 + 32 + lane;
+                const bool aa = pa < ncomp, ab = pb2 < ncomp;
+                const unsigned ca = aa ? S.cm[pa] : 0u, cb2 = ab ? S.cm[pb2] : 0u;
+                const int2 qa = pts[aa ? pa : 0], qb = pts[ab ? pb2 : 0];
+                const int fa = S.fr[(ca >> 8) & 31u].w, fb = S.fr[(cb2 >> 8) & 31u].w;   // e0 | e1 << 9 | ...
+                const int a0 = aa ? (fa & 0x1ff) : 0, a1 = aa ? ((fa >> 9) & 0x1ff) : 1;   // inactive: record 0
+                const int b0 = ab ? (fb & 0x1ff) : 0, b1 = ab ? ((fb >> 9) & 0x1ff) : 1;
+                const int K = __reduce_max_sync(FULL, (unsigned)max(a1 - a0, b1 - b0));
+                // nt = -sign(d_y) det exactly; the sign bit of (u_j ^ u_i) is the straddle test,
+                // u = p_y - y; a crossing counts when both sign bits are set
+                unsigned ada = rec_base + 16u * (unsigned)a0, adb = rec_base + 16u * (unsigned)b0;
+                const unsigned ala = rec_base + 16u * (unsigned)(a1 - 1), alb = rec_base + 16u * (unsigned)(b1 - 1);
+                const unsigned pxa = (unsigned)qa.x, pya = (unsigned)qa.y, pxb = (unsigned)qb.x, pyb = (unsigned)qb.y;
+                unsigned upa = pya - (unsigned)lds128(ala).w, upb = pyb - (unsigned)lds128(alb).w;   // vertex e0
+                unsigned acca = 0, accb = 0;
+                #pragma unroll 2
+                for (int k = 0; k < K; ++k) {
+                    const unsigned cura = ada, curb = adb;
+                    const int4 ra = lds128(ada), rb = lds128(adb);
+                    ada = __viaddmin_u32(ada, 16u, ala);
+                    adb = __viaddmin_u32(adb, 16u, alb);
+                    const unsigned ua = pya - (unsigned)ra.w, ub = pyb - (unsigned)rb.w;
+                    const unsigned nta = (unsigned)ra.x + pxa * (unsigned)ra.y + pya * (unsigned)ra.z;
+                    const unsigned ntb = (unsigned)rb.x + pxb * (unsigned)rb.y + pyb * (unsigned)rb.z;
+                    if (VERIFY) {   // straddling edges: their exact tests
+                        if (aa && (int)(ua ^ upa) < 0) {
+                            const int e = (int)((cura - rec_base) >> 4);
+                            const int2 ri = S.v[e], rj = S.v[e + 1 == a1 ? a0 : e + 1];
+                            st_err += exact_edge_counts(qa.x, qa.y, ri.x, ri.y, rj.x, rj.y) != (int)(nta >> 31);
+                            ++st_ver;
+                        }
+                        if (ab && (int)(ub ^ upb) < 0) {
+                            const int e = (int)((curb - rec_base) >> 4);
+                            const int2 ri = S.v[e], rj = S.v[e + 1 == b1 ? b0 : e + 1];
+                            st_err += exact_edge_counts(qb.x, qb.y, ri.x, ri.y, rj.x, rj.y) != (int)(ntb >> 31);
+                            ++st_ver;
+                        }
+                    }
+                    acca ^= (ua ^ upa) & nta;
+                    accb ^= (ub ^ upb) & ntb;
+                    upa = ua;
+                    upb = ub;
+                }
+                if (aa) S.par[ca & 0xffu] = (unsigned char)(acca >> 31);
+                if (ab) S.par[cb2 & 0xffu] = (unsigned char)(accb >> 31);
+            }
+        }
+        for (int r0 = 0; !set_all32 && r0 < ncomp; r0 += 32) {
             const int pos = r0 + lane;
             const bool act = pos < ncomp;
             const unsigned cmv = act ? S.cm[pos] : 0u;
@@ -434,33 +486,7 @@ __global__ void __launch_bounds__(SC_THREADS, 4) k_pip_cmp(ClassifyArgs a, Large
             const int fw = S.fr[(cmv >> 8) & 31u].w;   // e0 | e1 << 9 | mode << 18
             const int e0 = act ? (fw & 0x1ff) : 0, e1 = act ? ((fw >> 9) & 0x1ff) : 1;   // inactive: record 0 once
             int parity = 0;
-            if (set_all32) {
-                const int K = __reduce_max_sync(FULL, (unsigned)(e1 - e0));
-                // nt = -sign(d_y) det exactly; the sign bit of (u_j ^ u_i) is the straddle test,
-                // u = p_y - y; a crossing counts when both sign bits are set
-                unsigned ad = rec_base + 16u * (unsigned)e0;
-                const unsigned al = rec_base + 16u * (unsigned)(e1 - 1);
-                const unsigned px = (unsigned)p2.x, py = (unsigned)p2.y;
-                unsigned up = py - (unsigned)lds128(al).w;   // vertex e0
-                unsigned acc = 0;
-                #pragma unroll 4
-                for (int k = 0; k < K; ++k) {
-                    const unsigned acur = ad;
-                    const int4 q4 = lds128(ad);
-                    ad = __viaddmin_u32(ad, 16u, al);
-                    const unsigned u = py - (unsigned)q4.w;
-                    const unsigned nt = (unsigned)q4.x + px * (unsigned)q4.y + py * (unsigned)q4.z;
-                    if (VERIFY && act && (int)(u ^ up) < 0) {   // a straddling edge: its exact test
-                        const int e = (int)((acur - rec_base) >> 4);
-                        const int2 ri = S.v[e], rj = S.v[e + 1 == e1 ? e0 : e + 1];
-                        st_err += exact_edge_counts(p2.x, p2.y, ri.x, ri.y, rj.x, rj.y) != (int)(nt >> 31);
-                        ++st_ver;
-                    }
-                    acc ^= (u ^ up) & nt;
-                    up = u;
-                }
-                parity = (int)(acc >> 31);
-            } else {
+            {   // int64 / FP32 sets
                 const int4 f = S.fr[(cmv >> 8) & 31u];
                 const int mode = f.w >> 18;
                 const bool g6 = act && mode == MODE_INT64;

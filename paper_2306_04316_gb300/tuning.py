@@ -1,10 +1,12 @@
-"""Autotuner for pip_classify's large-polygon kernel (not part of the paper's method).
+"""Autotuner for pip_classify's kernels (not part of the paper's method).
 
-``autotune`` times ``pip_classify`` on the caller's device arrays for every tuning tuple
-(edge tile, candidates per thread, CTAs per SM) of a search grid, keeps the fastest, and stores
-it in a JSON cache keyed by the device name and a shape class of the workload, so that
-``apply_cached`` can set it for later calls without timing again.  The output bits do not
-depend on the tuning (every tuple is covered by the GPU parity tests); only speed does.
+``autotune`` times ``pip_classify`` on the caller's device arrays for every tuning tuple of the
+large-polygon kernel (edge tile, candidates per thread, CTAs per SM); ``autotune_small`` for
+every shape of the small-polygon kernel (lockstep or compacting kernel, candidates per slice,
+CTAs per SM).  Each keeps the fastest and stores it in a JSON cache keyed by the device name and
+a shape class of the workload, so that ``apply_cached`` can set both for later calls without
+timing again.  The output bits do not depend on the tuning (every tuple is covered by the GPU
+parity tests); only speed does.
 """
 from __future__ import annotations
 
@@ -13,6 +15,8 @@ import math
 import os
 
 DEFAULT_GRID = [(t, p, c) for t in (1024, 2048, 4096) for p in (1, 2, 4) for c in (2, 3, 4)]
+# small-polygon kernel: (kernel: 0 lockstep / 1 compacting, candidates per slice, CTAs per SM, 0 = all)
+SMALL_GRID = [(0, 256, 0), (0, 128, 0), (0, 256, 4), (1, 256, 0), (1, 128, 0), (1, 256, 3)]
 
 
 def cache_path() -> str:
@@ -52,15 +56,14 @@ def _key(device_name: str, cls: str) -> str:
     return f"{device_name}|{cls}"
 
 
-def autotune(points, poly_offsets, verts, cand_offsets=None, cand_ids=None, n_cands=None, grid=None, reps=5,
-             cache=True):
-    """Time pip_classify for every tuple of ``grid`` and apply the fastest; returns
-    ``(best_tuple, {tuple: ms})``."""
+def _search(set_fn, grid, points, poly_offsets, verts, cand_offsets, cand_ids, n_cands, reps, cache_field,
+            cache):
+    """Time pip_classify under each tuple of ``grid`` (applied by ``set_fn``), apply the fastest,
+    store it under ``cache_field`` of this device's and shape class's cache entry."""
     import torch
 
     from . import api
 
-    grid = grid or DEFAULT_GRID
     dense = cand_offsets is None
     n_polys = int(poly_offsets.shape[0]) - 1
     if not dense and n_cands is None:
@@ -71,7 +74,7 @@ def autotune(points, poly_offsets, verts, cand_offsets=None, cand_ids=None, n_ca
     stream = torch.cuda.current_stream()
     times = {}
     for t in grid:
-        api.pip_set_tuning(*t)
+        set_fn(*t)
         for _ in range(2):
             api.pip_classify(points, poly_offsets, verts, cand_offsets, cand_ids, out=out)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -82,14 +85,34 @@ def autotune(points, poly_offsets, verts, cand_offsets=None, cand_ids=None, n_ca
         e1.synchronize()
         times[t] = e0.elapsed_time(e1) / reps
     best = min(times, key=times.get)
-    api.pip_set_tuning(*best)
+    set_fn(*best)
     if cache:
         path = cache_path()
         c = _load_cache(path)
         cls = shape_class(n_polys, int(verts.shape[0]), n_c, dense)
-        c[_key(torch.cuda.get_device_name(points.device), cls)] = {"tuning": list(best), "ms": times[best]}
+        entry = c.setdefault(_key(torch.cuda.get_device_name(points.device), cls), {})
+        entry[cache_field] = list(best)
+        entry[cache_field + "_ms"] = times[best]
         _store_cache(path, c)
     return best, times
+
+
+def autotune(points, poly_offsets, verts, cand_offsets=None, cand_ids=None, n_cands=None, grid=None, reps=5,
+             cache=True):
+    """Time pip_classify for every large-polygon tuple of ``grid`` and apply the fastest; returns
+    ``(best_tuple, {tuple: ms})``."""
+    from . import api
+    return _search(api.pip_set_tuning, grid or DEFAULT_GRID, points, poly_offsets, verts, cand_offsets, cand_ids,
+                   n_cands, reps, "tuning", cache)
+
+
+def autotune_small(points, poly_offsets, verts, cand_offsets=None, cand_ids=None, n_cands=None, grid=None,
+                   reps=5, cache=True):
+    """Time pip_classify for every small-polygon kernel shape of ``grid`` and apply the fastest;
+    returns ``(best_tuple, {tuple: ms})``."""
+    from . import api
+    return _search(api.pip_set_small_tuning, grid or SMALL_GRID, points, poly_offsets, verts, cand_offsets,
+                   cand_ids, n_cands, reps, "small", cache)
 
 
 def apply_cached(n_polys: int, n_vertices: int, n_candidates: int, dense: bool, device_name: str):
@@ -99,6 +122,10 @@ def apply_cached(n_polys: int, n_vertices: int, n_candidates: int, dense: bool, 
     c = _load_cache(cache_path())
     entry = c.get(_key(device_name, shape_class(n_polys, n_vertices, n_candidates, dense)))
     if not entry:
+        return None
+    if "small" in entry:
+        api.pip_set_small_tuning(*[int(x) for x in entry["small"]])
+    if "tuning" not in entry:
         return None
     t = tuple(int(x) for x in entry["tuning"])
     api.pip_set_tuning(*t)

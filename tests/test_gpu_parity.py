@@ -657,7 +657,8 @@ def _small_kernel_cases():
     return cases
 
 
-@pytest.mark.parametrize("small", [(0, 256, 0), (1, 256, 0), (1, 128, 0), (1, 256, 1), (1, 128, 2)])
+@pytest.mark.parametrize("small", [(0, 256, 0), (0, 128, 0), (0, 256, 3), (1, 256, 0), (1, 128, 0), (1, 256, 1),
+                                   (1, 128, 2)])
 def test_small_kernel_shapes(api, small):
     """Both small-polygon kernels and every slice size give the oracle's bits."""
     before = api.pip_get_small_tuning()

@@ -53,3 +53,33 @@ def test_autotune_on_gpu(tmp_path, monkeypatch):
         assert tuning.apply_cached(w.n_polys, w.verts.shape[0], w.n_bits, False, name) == best
     finally:
         api.pip_set_tuning(*before)
+
+
+@pytest.mark.gpu
+def test_autotune_small_on_gpu(tmp_path, monkeypatch):
+    """The small-polygon kernel's tuner: every shape of its grid timed, the fastest applied and
+    cached, and the bits unchanged."""
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2306_04316_gb300 import api, workloads as W
+    monkeypatch.setenv("PIP_TUNING_CACHE", str(tmp_path / "t.json"))
+    before = api.pip_get_small_tuning()
+    try:
+        w = W.footprints(seed=93, n_polys=20_000, pts_per_poly=16)
+        d = api.to_device(w)
+        ref = api.pip_classify(d["points"], d["poly_offsets"], d["verts"], d["cand_offsets"], d["cand_ids"],
+                               n_cands=w.n_bits).clone()
+        best, times = tuning.autotune_small(d["points"], d["poly_offsets"], d["verts"], d["cand_offsets"],
+                                            d["cand_ids"], n_cands=w.n_bits, reps=2)
+        assert best in tuning.SMALL_GRID and set(times) == set(tuning.SMALL_GRID)
+        assert api.pip_get_small_tuning() == best
+        got = api.pip_classify(d["points"], d["poly_offsets"], d["verts"], d["cand_offsets"], d["cand_ids"],
+                               n_cands=w.n_bits)
+        torch.cuda.synchronize()
+        assert torch.equal(got, ref)
+        api.pip_set_small_tuning(*before)
+        tuning.apply_cached(w.n_polys, w.verts.shape[0], w.n_bits, False, torch.cuda.get_device_name(0))
+        assert api.pip_get_small_tuning() == best
+    finally:
+        api.pip_set_small_tuning(*before)
