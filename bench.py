@@ -638,14 +638,27 @@ def other_configs(args, peaks, peak_kind, n_sm):
     import gc
     import torch
     from paper_2306_04316_gb300 import api
+    from paper_2306_04316_gb300 import tuning
     res = {}
     stream = torch.cuda.Stream()
+    small0, large0 = api.pip_get_small_tuning(), api.pip_get_tuning()
+    large_grid = [(2048, 4, 3), (4096, 4, 3), (4096, 4, 2)]
     for name, steps in (("star", 20), ("stress", 20), ("fractal", 4), ("country", 3)):
         w = make_workload(name, 0, 1.0)
         T, B = w.pair_tests(), w.algorithmic_bytes()
         d = api.to_device(w)
         out = torch.empty(w.n_words, dtype=torch.int32, device="cuda")
         co, ci = d.get("cand_offsets"), d.get("cand_ids")
+        # each workload's kernel shapes picked on its own batch: the small-polygon kernel always,
+        # the large-polygon kernel's tuning where its polygons carry the work
+        n_c = None if w.dense else w.n_bits
+        api.pip_set_small_tuning(*small0)
+        api.pip_set_tuning(*large0)
+        tuned = {"small": list(tuning.autotune_small(d["points"], d["poly_offsets"], d["verts"], co, ci,
+                                                     n_cands=n_c, reps=3, cache=False)[0])}
+        if name in ("star", "fractal", "country"):
+            tuned["large"] = list(tuning.autotune(d["points"], d["poly_offsets"], d["verts"], co, ci, n_cands=n_c,
+                                                  grid=large_grid, reps=2, cache=False)[0])
 
         def call():
             api.pip_classify(d["points"], d["poly_offsets"], d["verts"], co, ci, out=out)
@@ -659,10 +672,12 @@ def other_configs(args, peaks, peak_kind, n_sm):
                      "roofline": {k: roof[k] for k in ("bound", "achieved", "peak", "unit", "frac")},
                      "dtype": arithmetic_of(w),
                      "fallback_fraction": stt["fallback_points"] / stt["candidates"] if stt["candidates"] else None,
-                     "wait_timeouts": stt["wait_timeouts"]}
+                     "wait_timeouts": stt["wait_timeouts"], "autotuned": tuned}
         del d, out, w
         gc.collect()
         torch.cuda.empty_cache()
+    api.pip_set_small_tuning(*small0)
+    api.pip_set_tuning(*large0)
     jargs = argparse.Namespace(**vars(args))
     jargs.steps, jargs.warmup, jargs.scale = 3, 3, 1.0
     jl = run_join(jargs, 0, 1, quiet=True)
@@ -670,7 +685,9 @@ def other_configs(args, peaks, peak_kind, n_sm):
                    "pair_tests_per_s": jl["value"], "points_per_s": jl["points_per_s"],
                    "binning_ms_per_step": jl["config"]["binning_ms_per_step"],
                    "roofline": {k: jl["roofline"][k] for k in ("bound", "achieved", "peak", "unit", "frac")},
-                   "dtype": jl["dtype"]}
+                   "dtype": jl["dtype"], "autotuned": jl["config"]["autotuned"]}
+    api.pip_set_small_tuning(*small0)
+    api.pip_set_tuning(*large0)
     gc.collect()
     torch.cuda.empty_cache()
     return res

@@ -497,8 +497,9 @@ __device__ __forceinline__ void tile_parity_multi(const float4 *__restrict__ s_r
                                                   int oy, int (&par)[PPT], unsigned long long &n_fb_pts,
                                                   unsigned long long &n_err, unsigned long long &n_ver)
 {
-    // one candidate at a time: the side of the previous vertex is carried in one predicate
-    #pragma unroll 1
+    // one candidate at a time: the side of the previous vertex is carried in one predicate (the
+    // loop is unrolled so that the thread's candidate arrays stay in registers)
+    #pragma unroll
     for (int r = 0; r < PPT; ++r) {
         if (!ok[r]) continue;
         const float Px = __ll2float_rn((long long)p[r].x - ox);
@@ -555,7 +556,7 @@ __device__ __forceinline__ void tile_parity_scaled(const int4 *__restrict__ s_re
         acc[r] = 0;
         unc[r] = 0;
     }
-    #pragma unroll 2
+    #pragma unroll 4
     for (int e = 0; e < nt; ++e) {
         const int4 q = s_rec[e];
         const float rc = __int_as_float(q.x), ra = __int_as_float(q.y), rb = __int_as_float(q.z);
