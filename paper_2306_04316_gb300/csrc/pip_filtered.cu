@@ -33,9 +33,10 @@
 // No filter and no recheck are needed for such polygons (building footprints, parcels).
 //
 // Exact int64 evaluation.  When the box is below 2^31 on both sides but too large for int32,
-// the record (X_i, Y_i, s d_x, d_y) holds int32 values in the box-centre frame and
-// nt = (P_x - X_i)|d_y| + (Y_i - P_y) s d_x = -s det is formed exactly from two 32 x 32 -> 64-bit
-// products (every factor below 2^31): again no filter and no recheck.  A run with any polygon
+// the record (X_i, |d_y|, -s d_x, Y_j) holds int32 values in the box-centre frame and
+// nt = (P_x - X_i)|d_y| + (P_y - Y_i)(-s d_x) = -s det is formed exactly from two 32 x 32 -> 64-bit
+// products (every factor below 2^31; P_y - Y_i is the previous step's P_y - Y_j): again no filter
+// and no recheck.  A run with any polygon
 // outside the int32 test puts all its polygons on the int64 or FP32 test, so the lanes of a
 // round walk at most two kinds of loop.  Only boxes of 2^31 or more use the FP32 filter.
 //
@@ -307,10 +308,10 @@ __global__ void __launch_bounds__(WP_THREADS, WP_CTAS) k_pip_warp(ClassifyArgs a
                             const int e0 = f.w & 0x1ff, e1 = (f.w >> 9) & 0x1ff, md = f.w >> 18;
                             const int2 ri = S.v[i], rj = S.v[i + 1 == e1 ? e0 : i + 1];
                             if (md == MODE_INT64) {
-                                // (X_i, Y_i, s d_x, d_y), s = sign(d_y); every value below 2^31
+                                // (X_i, |d_y|, -s d_x, Y_j), s = sign(d_y); every value below 2^31
                                 const int dx = rj.x - ri.x, dy = rj.y - ri.y;
                                 reinterpret_cast<int4 *>(S.rec)[i] =
-                                    make_int4(ri.x - f.x, ri.y - f.y, dy > 0 ? dx : -dx, dy);
+                                    make_int4(ri.x - f.x, dy > 0 ? dy : -dy, dy > 0 ? -dx : dx, rj.y - f.y);
                             } else if (md == MODE_FP32) {
                                 S.rec[i] = fp32_record(ri, rj, f.x, f.y);
                             } else {
@@ -376,23 +377,22 @@ __global__ void __launch_bounds__(WP_THREADS, WP_CTAS) k_pip_warp(ClassifyArgs a
                         const bool g6 = go && mode == MODE_INT64;
                         const int k6 = __reduce_max_sync(FULL, g6 ? e1 - e0 : 0);
                         if (k6 > 0) {
-                            // record (X_i, Y_i, s d_x, d_y) in the frame; u = P_y - y: the straddle test is
-                            // the sign bit of u_i ^ u_j, and nt = (P_x - X_i)|d_y| + (Y_i - P_y) s d_x =
-                            // -s det in int64 (every factor below 2^31); a crossing counts when the
-                            // straddle bit and nt's sign bit are both set
+                            // record (X_i, |d_y|, -s d_x, Y_j) in the frame; u = P_y - y, u_i carried from the
+                            // step before and u_j from the record (so a repeated record adds nothing): the straddle
+                            // test is the sign bit of u_i ^ u_j, and nt = (P_x - X_i)|d_y| + u_i (-s d_x) = -s det in
+                            // int64 (every factor below 2^31); a crossing counts when both sign bits are set
                             unsigned ad = rec_base + 16u * (unsigned)(g6 ? e0 : 0);
                             const unsigned al = rec_base + 16u * (unsigned)(g6 ? e1 - 1 : 0);
                             const unsigned Px = (unsigned)p2.x - (unsigned)f.x, Py = (unsigned)p2.y - (unsigned)f.y;
-                            unsigned up = Py - (unsigned)lds128(ad).y;   // vertex e0
+                            unsigned up = Py - (unsigned)lds128(al).w;   // vertex e0 (end of the closing edge)
                             unsigned acc = 0;
                             #pragma unroll 2
                             for (int k = 0; k < k6; ++k) {
                                 const int4 q4 = lds128(ad);
                                 ad = __viaddmin_u32(ad, 16u, al);
-                                const unsigned ui = Py - (unsigned)q4.y;              // P_y - Y_i
-                                const unsigned uj = ui - (unsigned)q4.w;              // P_y - Y_j
-                                const long long nt = (long long)(int)(Px - (unsigned)q4.x) * (long long)abs(q4.w) -
-                                                     (long long)(int)ui * (long long)q4.z;
+                                const unsigned uj = Py - (unsigned)q4.w;   // P_y - Y_j; P_y - Y_i is up
+                                const long long nt = (long long)(int)(Px - (unsigned)q4.x) * (long long)q4.y +
+                                                     (long long)(int)up * (long long)q4.z;
                                 acc ^= (up ^ uj) & (unsigned)((unsigned long long)nt >> 32);
                                 up = uj;
                             }
