@@ -201,6 +201,7 @@ def _threaded_sample(w, sample, threads):
 
 
 KERNEL_SOURCES = ["paper_2306_04316_gb300/csrc/pip_filtered.cu", "paper_2306_04316_gb300/csrc/pip_small.cu",
+                  "paper_2306_04316_gb300/csrc/pip_tpp.cu",
                   "paper_2306_04316_gb300/csrc/pip_edge.cuh", "paper_2306_04316_gb300/csrc/pip_device.cuh",
                   "paper_2306_04316_gb300/csrc/pip_launch.h"]
 

@@ -286,8 +286,12 @@ int pip_get_tuning(int32_t *edge_tile, int32_t *pts_per_thread, int32_t *ctas_pe
  *   kernel       0 (default) = lockstep kernel: every candidate walks its polygon's edges in
  *                rounds of 32 consecutive candidates; 1 = compacting kernel: the candidates of a
  *                slice that lie inside their polygon's box are packed together before the edge
- *                walk, and each slice's loads are issued one slice ahead; -1 keeps the value
- *   slice        candidates per slice (both kernels), 128 or 256 (default); 0 keeps it
+ *                walk, and each slice's loads are issued one slice ahead; 2 = thread-per-polygon
+ *                kernel: a thread walks its polygon's edges once for a block of candidates held
+ *                in registers (clamped to the polygon's box, which keeps the parity), the
+ *                polygons of a CTA sorted by vertex count; -1 keeps the value
+ *   slice        candidates per slice (kernels 0 and 1), 128 or 256 (default); kernel 2 takes
+ *                slice / 16 candidates per thread (8 or 16); 0 keeps it
  *   ctas_per_sm  resident CTAs per SM of either kernel's persistent grid, 1..16, 0 = as many as
  *                fit (default); -1 keeps it
  * Applies to later calls on every device; PIP_ERR_INVALID for an out-of-range value.

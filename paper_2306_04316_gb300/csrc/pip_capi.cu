@@ -283,7 +283,7 @@ int pip_set_tuning(int32_t edge_tile, int32_t pts_per_thread, int32_t ctas_per_s
 
 int pip_set_small_tuning(int32_t kernel, int32_t slice, int32_t ctas_per_sm)
 {
-    if (kernel < -1 || kernel > 1) return PIP_ERR_INVALID;
+    if (kernel < -1 || kernel > 2) return PIP_ERR_INVALID;
     if (slice != 0 && slice != 128 && slice != 256) return PIP_ERR_INVALID;
     if (ctas_per_sm < -1 || ctas_per_sm > 16) return PIP_ERR_INVALID;
     if (kernel >= 0) g_small_kernel.store(kernel);

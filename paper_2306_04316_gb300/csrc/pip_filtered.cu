@@ -1011,6 +1011,8 @@ static int launch_filtered_v(const ClassifyArgs &a, long long total_bits, const 
     int e;
     if (t.small_kernel == 1)
         e = launch_small_cmp(a, ll, lcap, n_sm, t.small_slice, t.small_ctas, VERIFY, stream);
+    else if (t.small_kernel == 2)
+        e = launch_small_tpp(a, ll, lcap, n_sm, t.small_slice / 16, t.small_ctas, VERIFY, stream);
     else
         e = a.cand_offsets ? launch_warp_d<false, VERIFY>(a, ll, lcap, n_sm, t.small_slice, t.small_ctas, stream)
                            : launch_warp_d<true, VERIFY>(a, ll, lcap, n_sm, t.small_slice, t.small_ctas, stream);

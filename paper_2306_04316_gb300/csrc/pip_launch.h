@@ -28,9 +28,10 @@ struct Tuning {
     int pts_per_thread;  // large-polygon kernel: candidates carried by each thread (1, 2, 4)
     int ctas_per_sm;     // large-polygon kernel: resident CTAs per SM
     int verify;          // recheck every trusted decision exactly and count disagreements
-    int small_kernel;    // small polygons: 0 = lockstep rounds (k_pip_warp), 1 = compacting (k_pip_cmp)
-    int small_slice;     // compacting kernel: candidates per slice (128, 256)
-    int small_ctas;      // compacting kernel: resident CTAs per SM (0 = as many as fit)
+    int small_kernel;    // small polygons: 0 = lockstep rounds (k_pip_warp), 1 = compacting (k_pip_cmp),
+                         // 2 = thread per polygon (k_pip_tpp)
+    int small_slice;     // kernels 0 and 1: candidates per slice (128, 256); kernel 2: slice / 16 per thread
+    int small_ctas;      // small-polygon kernel: resident CTAs per SM (0 = as many as fit)
 };
 
 int launch_exact(const ClassifyArgs &a, long long total_bits, int grid, cudaStream_t stream, int rule = 0);
@@ -38,6 +39,8 @@ int launch_filtered(const ClassifyArgs &a, long long total_bits, const Tuning &t
                     int lcap, cudaStream_t stream);
 size_t filtered_smem_bytes(int edge_tile);
 int launch_small_cmp(const ClassifyArgs &a, LargeList *ll, int lcap, int n_sm, int slice, int ctas_per_sm,
+                     bool verify, cudaStream_t stream);
+int launch_small_tpp(const ClassifyArgs &a, LargeList *ll, int lcap, int n_sm, int block, int ctas_per_sm,
                      bool verify, cudaStream_t stream);
 Tuning current_tuning();   // the values set by pip_set_tuning
 int launch_validate(const ClassifyArgs &a, long long n_verts, long long n_cand_ids, int *d_status, int grid,

@@ -2,8 +2,8 @@
 
 ``autotune`` times ``pip_classify`` on the caller's device arrays for every tuning tuple of the
 large-polygon kernel (edge tile, candidates per thread, CTAs per SM); ``autotune_small`` for
-every shape of the small-polygon kernel (lockstep or compacting kernel, candidates per slice,
-CTAs per SM).  Each keeps the fastest and stores it in a JSON cache keyed by the device name and
+every shape of the small-polygon kernel (lockstep, compacting or thread-per-polygon kernel,
+candidates per slice, CTAs per SM).  Each keeps the fastest and stores it in a JSON cache keyed by the device name and
 a shape class of the workload, so that ``apply_cached`` can set both for later calls without
 timing again.  The output bits do not depend on the tuning (every tuple is covered by the GPU
 parity tests); only speed does.
@@ -15,8 +15,10 @@ import math
 import os
 
 DEFAULT_GRID = [(t, p, c) for t in (1024, 2048, 4096) for p in (1, 2, 4) for c in (2, 3, 4)]
-# small-polygon kernel: (kernel: 0 lockstep / 1 compacting, candidates per slice, CTAs per SM, 0 = all)
-SMALL_GRID = [(0, 256, 0), (0, 128, 0), (0, 256, 4), (1, 256, 0), (1, 128, 0), (1, 256, 3)]
+# small-polygon kernel: (kernel: 0 lockstep / 1 compacting / 2 thread per polygon, candidates per slice
+# (kernel 2: slice / 16 per thread), CTAs per SM, 0 = all)
+SMALL_GRID = [(0, 256, 0), (0, 128, 0), (0, 256, 4), (1, 256, 0), (1, 128, 0), (1, 256, 3), (2, 256, 0),
+              (2, 128, 0)]
 
 
 def cache_path() -> str:

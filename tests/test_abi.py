@@ -90,7 +90,7 @@ def test_tuning_validation(lib):
     assert lib.pip_set_tuning(0, 3, 0) == _lib.PIP_ERR_INVALID
     assert lib.pip_set_tuning(0, 0, 9) == _lib.PIP_ERR_INVALID
     assert lib.pip_set_tuning(1024, 4, 2) == 0
-    assert lib.pip_set_small_tuning(2, 0, -1) == _lib.PIP_ERR_INVALID    # no such kernel
+    assert lib.pip_set_small_tuning(3, 0, -1) == _lib.PIP_ERR_INVALID    # no such kernel
     assert lib.pip_set_small_tuning(-1, 64, -1) == _lib.PIP_ERR_INVALID  # slice 128 or 256
     assert lib.pip_set_small_tuning(-1, 0, 17) == _lib.PIP_ERR_INVALID
     assert lib.pip_get_tuning(*[ctypes.byref(x) for x in t]) == 0

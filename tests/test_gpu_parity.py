@@ -654,13 +654,52 @@ def _small_kernel_cases():
         parts.append(W.fractal(seed=70 + i, n_polys=1, m_lo=300 + 500 * i, m_hi=301 + 500 * i,
                                n_points=900 + 77 * i, cell=100_000, grid=1))
     cases.append(_concat(parts, "interleaved"))
+    cases.append(_extreme_small_case(rng))
     return cases
 
 
+def _extreme_small_case(rng):
+    """Small polygons whose pair tests sit at the limits of the 32-bit arithmetic: boxes at the
+    corners of the int32 range against points anywhere in it (differences that wrap), boxes with
+    (W + 1)(H + 1) exactly 2^30 and just above (the int32 test's bound), thin boxes of width about
+    2^29, and polygons of 0, 1 and 2 vertices; candidates on vertices, edges and box sides."""
+    I0, I1 = -2**31, 2**31 - 1
+    polys, csr, pts = [], [], []
+
+    def add(poly, extra):
+        ids = []
+        xs = [v[0] for v in poly] or [0]
+        ys = [v[1] for v in poly] or [0]
+        near = [(int(np.clip(x, I0, I1)), int(np.clip(y, I0, I1))) for x, y in zip(
+            rng.integers(min(xs) - 3, max(xs) + 4, 24), rng.integers(min(ys) - 3, max(ys) + 4, 24))]
+        for q in list(poly) + near + extra + [pts[int(i)] for i in rng.integers(0, max(1, len(pts)), 6) if pts]:
+            ids.append(len(pts))
+            pts.append(q)
+        polys.append(poly)
+        csr.append(ids)
+
+    far = [tuple(int(c) for c in q) for q in rng.integers(I0, I1, (40, 2), endpoint=True)]
+    for cx, cy in [(I0, I0), (I0, I1 - 40), (I1 - 40, I0), (I1 - 40, I1 - 40)]:
+        for _ in range(6):
+            m = int(rng.integers(3, 12))
+            add([(cx + int(rng.integers(0, 41)), cy + int(rng.integers(0, 41))) for _ in range(m)], far)
+    for w1, h1 in [(2**15, 2**15), (2**15 + 1, 2**15), (2**29, 2), (2**29 + 1, 2), (2**30, 1), (1, 2**30)]:
+        W_, H_ = w1 - 1, h1 - 1
+        x0, y0 = int(rng.integers(-2**30, 2**29)), int(rng.integers(-2**30, 2**29))
+        poly = [(x0, y0), (x0 + W_ // 2, y0 + H_ // 3), (x0 + W_, y0), (x0 + W_, y0 + H_), (x0 + W_ // 3, y0 + H_ // 2),
+                (x0, y0 + H_)]
+        add(poly, [(x0 + W_ // 2, y0 + H_ // 2), (x0 - 1, y0 + H_ // 2), (x0 + W_ + 1, y0 + H_ // 2)] + far[:10])
+    for m in (0, 1, 2, 0, 2, 1):
+        add([(int(rng.integers(-50, 50)), int(rng.integers(-50, 50))) for _ in range(m)], far[:5])
+    return make("extremes", polys, pts, csr)
+
+
 @pytest.mark.parametrize("small", [(0, 256, 0), (0, 128, 0), (0, 256, 3), (1, 256, 0), (1, 128, 0), (1, 256, 1),
-                                   (1, 128, 2)])
+                                   (1, 128, 2), (2, 256, 0), (2, 128, 0), (2, 256, 1), (2, 128, 3)],
+                         ids=lambda s: "k%d-%d-%d" % s)
 def test_small_kernel_shapes(api, small):
-    """Both small-polygon kernels and every slice size give the oracle's bits."""
+    """Every small-polygon kernel, slice size (candidates per thread) and CTA count gives the
+    oracle's bits."""
     before = api.pip_get_small_tuning()
     api.pip_set_small_tuning(*small)
     try:
