@@ -206,6 +206,9 @@ KERNEL_SOURCES = ["paper_2306_04316_gb300/csrc/pip_filtered.cu", "paper_2306_043
                   "paper_2306_04316_gb300/csrc/pip_launch.h"]
 
 
+SMALL_KERNEL_NAMES = {0: "k_pip_warp", 1: "k_pip_cmp", 2: "k_pip_tpp"}   # pip_set_small_tuning's kernels
+
+
 def kernel_source_hash():
     import hashlib
     h = hashlib.sha256()
@@ -922,7 +925,7 @@ def main():
     props = torch.cuda.get_device_properties(local)
     n_sm = props.multi_processor_count
     achieved_gbs = B / (kern_ms / 1000.0) / 1e9
-    small_name = "k_pip_cmp" if api.pip_get_small_tuning()[0] == 1 else "k_pip_warp"
+    small_name = SMALL_KERNEL_NAMES.get(api.pip_get_small_tuning()[0], "k_pip_warp")
     traffic = profiled_traffic(args.workload, small_name) if args.kernel == "filtered" and args.scale == 1.0 else None
     roof = roofline_of(T, B, kern_ms, peaks, peak_kind, n_sm,
                        f"{small_name} + k_pip_large" if args.kernel == "filtered" else "k_pip_exact", traffic)

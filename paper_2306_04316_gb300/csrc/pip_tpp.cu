@@ -252,7 +252,7 @@ __global__ void __launch_bounds__(TP_THREADS) k_pip_tpp(ClassifyArgs a, LargeLis
                 const int2 q = __ldg(V + e);
                 x0 = min(x0, q.x); y0 = min(y0, q.y); x1 = max(x1, q.x); y1 = max(y1, q.y);
             }
-            unsigned valid = 0;
+            unsigned valid = 0, inm = 0;
             int px[NB], py[NB];
             #pragma unroll
             for (int j = 0; j < NB; ++j) {
@@ -263,10 +263,12 @@ __global__ void __launch_bounds__(TP_THREADS) k_pip_tpp(ClassifyArgs a, LargeLis
                     px[j] = p.x;
                     py[j] = p.y;
                     valid |= 1u << j;
-                    st_in += p.x >= x0 && p.x <= x1 && p.y >= y0 && p.y <= y1;
+                    inm |= (unsigned)(p.x >= x0 && p.x <= x1 && p.y >= y0 && p.y <= y1) << j;
                 }
             }
+            asm volatile("" : "+r"(inm));   // the box test here: the raw points need not outlive the clamp
             st_cand += __popc(valid);
+            st_in += __popc(inm);
             const unsigned W = (unsigned)x1 - (unsigned)x0, H = (unsigned)y1 - (unsigned)y0;
             unsigned bits = 0;
             if (W < (1u << 30) && H < (1u << 30) && (W + 1ULL) * (H + 1ULL) <= (1ULL << 30)) {
@@ -280,28 +282,31 @@ __global__ void __launch_bounds__(TP_THREADS) k_pip_tpp(ClassifyArgs a, LargeLis
                     py[j] = min(py[j] < y0 ? y0 - 1 : py[j], y1);
                 }
                 int2 ri = __ldg(V + mv - 1);
-                unsigned u[NB], acc[NB];
+                // NB = 16: p_y - y_i recomputed per edge instead of carried (16 registers fewer)
+                constexpr bool CARRY = NB <= 8;
+                unsigned u[CARRY ? NB : 1], acc[NB];
                 #pragma unroll
                 for (int j = 0; j < NB; ++j) {
-                    u[j] = (unsigned)py[j] - (unsigned)ri.y;
+                    if (CARRY) u[j] = (unsigned)py[j] - (unsigned)ri.y;
                     acc[j] = 0;
                 }
                 // edge ri -> rj: nt = c + p_x a + p_y b = -sign(d_y) det (exact), u = p_y - y; the
                 // crossing counts when the sign bits of u_i ^ u_j (straddle) and nt are both set
-                #pragma unroll 2
+                #pragma unroll CARRY ? 2 : 1
                 for (int e = 0; e < mv; ++e) {
                     const int2 rj = __ldg(V + e);
                     const int4 r = int32_record(ri, rj);
                     #pragma unroll
                     for (int j = 0; j < NB; ++j) {
                         const unsigned uj = (unsigned)py[j] - (unsigned)rj.y;
+                        const unsigned ui = CARRY ? u[CARRY ? j : 0] : (unsigned)py[j] - (unsigned)ri.y;
                         const unsigned nt = (unsigned)r.x + (unsigned)px[j] * (unsigned)r.y + (unsigned)py[j] * (unsigned)r.z;
-                        if (VERIFY && ((valid >> j) & 1u) && (int)(u[j] ^ uj) < 0) {
+                        if (VERIFY && ((valid >> j) & 1u) && (int)(ui ^ uj) < 0) {
                             st_err += exact_edge_counts(ox[j], oy[j], ri.x, ri.y, rj.x, rj.y) != (int)(nt >> 31);
                             ++st_ver;
                         }
-                        acc[j] ^= (u[j] ^ uj) & nt;
-                        u[j] = uj;
+                        acc[j] ^= (ui ^ uj) & nt;
+                        if (CARRY) u[CARRY ? j : 0] = uj;
                     }
                     ri = rj;
                 }

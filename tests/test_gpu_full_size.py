@@ -5,6 +5,7 @@ configuration that bench.py times; every bit is compared with the oracle (0 mism
   (test_gpu_parity.test_star_full), the fractal batch (64 polygons of 1e4-1e6 vertices, 10M
   points, about 8e11 pair tests) and the paper-shaped country batch (17,097,823 points against
   one 100,000-vertex polygon, dense): all bits, both kernels;
+- footprints and stress again under every small-polygon kernel shape of the autotuner's grid;
 - the spatial join (100k polygons against one full 10M-point batch): the GPU candidate lists
   must equal the closed-box lists computed here from the definition on points sorted by x
   (that computation is itself checked against the oracle's brute-force join on 100 polygons),
@@ -30,6 +31,23 @@ def test_footprints_full_size(api):
 
 def test_stress_full_size(api):
     check_full(api, W.stress(), "full size")
+
+
+@pytest.mark.parametrize("make", [W.footprints, W.stress], ids=["footprints", "stress"])
+def test_full_size_every_small_kernel(api, make):
+    """Every small-polygon kernel shape the autotuner may pick for the timed step (lockstep,
+    compacting, thread per polygon; each slice size and CTA count of its grid) gives the oracle's
+    bits on the full footprint and stress batches."""
+    from paper_2306_04316_gb300 import tuning
+    w = make()
+    want = oracle.classify(w.points, w.poly_offsets, w.verts, w.cand_offsets, w.cand_ids)
+    before = api.pip_get_small_tuning()
+    try:
+        for shape in tuning.SMALL_GRID:
+            api.pip_set_small_tuning(*shape)
+            assert_same(gpu_bits(api, w), want, w.n_bits, f"{w.name} full size small={shape}")
+    finally:
+        api.pip_set_small_tuning(*before)
 
 
 def test_fractal_full_size(api):
