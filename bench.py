@@ -396,10 +396,12 @@ def run_join(args, rank, world, quiet=False):
         one_pass()
     stream.synchronize()
     assert int(ovf.sum().item()) == 0
-    # the large-polygon kernel's tuning, picked by the autotuner on the first batch
+    # the small- and large-polygon kernels' shapes, picked by the autotuner on the first batch
     from paper_2306_04316_gb300 import tuning
+    best_s, times_s = tuning.autotune_small(d_pts[0], d_po, d_v, co[0], ids[0], n_cands=totals[0], cache=False)
     best, times = tuning.autotune(d_pts[0], d_po, d_v, co[0], ids[0], n_cands=totals[0], cache=False)
-    autotuned = {"best": list(best), "candidates": len(times), "best_ms": times[best]}
+    autotuned = {"best": list(best), "candidates": len(times), "best_ms": times[best],
+                 "small": {"best": list(best_s), "candidates": len(times_s), "best_ms": times_s[best_s]}}
     m = np.diff(po.astype(np.int64))
     T = sum(int((m * np.diff(c.cpu().numpy().astype(np.int64))).sum()) for c in co)
     C = sum(int(c[-1].item()) for c in co)
@@ -494,12 +496,13 @@ def run_join(args, rank, world, quiet=False):
                                        f"({ns} streams)",
                            "pair_tests_per_step": T, "candidates_per_step": C, "binning_ms_per_step": bin_ms,
                            "classify_ms_per_step": ms - bin_ms, "tuning": list(api.pip_get_tuning()),
+                           "small_tuning": list(api.pip_get_small_tuning()),
                            "autotuned": autotuned, "l2": "inputs larger than L2 (no flush)"},
                 "points_per_s": job_rate(nb * n_pts * world, ms), "cpu_baseline": cpu, "clocks": clocks,
                 "gpu_launches": per_replay["full"] * args.steps,
                 "roofline": {"bound": "hbm", "achieved": join_bytes / (ms / 1000.0) / 1e9, "peak": hbm,
                              "unit": "GB/s", "frac": join_bytes / (ms / 1000.0) / 1e9 / hbm, "traffic": None,
-                             "peak_source": peak_kind, "kernel": "binning + k_pip_warp + k_pip_large (whole step)",
+                             "peak_source": peak_kind, "kernel": f"binning + {SMALL_KERNEL_NAMES.get(best_s[0], 'k_pip_warp')} + k_pip_large (whole step)",
                              "algorithmic_bytes": join_bytes, "kernel_ms": ms},
                 "e2e": e2e}
         if quiet:
