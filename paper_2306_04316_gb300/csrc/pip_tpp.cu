@@ -68,7 +68,7 @@ constexpr int TP_OB = 1024;               // output words staged per group
 
 template <typename CI>
 struct TppSmem {
-    unsigned long long hist[TP_KEYS];     // per key: items (low 32 bits), polygons (high 32 bits)
+    unsigned hist[TP_KEYS];               // per key: items (low 24 bits), polygons (high 8 bits)
     CI cb[TP_G];                          // first output bit of each polygon's candidates
     int pb[TP_G];                         // first vertex
     int m[TP_G];                          // vertices
@@ -125,7 +125,7 @@ __global__ void __launch_bounds__(TP_THREADS) k_pip_tpp(ClassifyArgs a, LargeLis
 
     // the histogram is zero at the start of every group: cleared here, and again by each group
     // after its last read (two barriers before the next group's counts)
-    for (int i = t; i < TP_KEYS; i += TP_THREADS) S.hist[i] = 0ULL;
+    for (int i = t; i < TP_KEYS; i += TP_THREADS) S.hist[i] = 0u;
     __syncthreads();
     for (int g = blockIdx.x; g < ngroups; g += gridDim.x) {
         const int k0 = g * TP_G, np = min(TP_G, P - k0);
@@ -135,7 +135,7 @@ __global__ void __launch_bounds__(TP_THREADS) k_pip_tpp(ClassifyArgs a, LargeLis
         CI cb = 0, ce = 0;
         bool zr = false;                       // bits to zero here (CSR): a large or empty polygon
         bool sorted = false;                   // the polygon has items
-        unsigned long long slot = 0;           // its place in its key's bucket
+        unsigned slot = 0;                     // its place in its key's bucket
         if (t < np) {
             const int k = k0 + t;
             const int pb = __ldg(a.poly_offsets + k);
@@ -163,7 +163,7 @@ __global__ void __launch_bounds__(TP_THREADS) k_pip_tpp(ClassifyArgs a, LargeLis
                 n = (int)nlen;                 // below 2^18 when m > 0
                 if (m > 0) {
                     const unsigned nb = (unsigned)((n + NB - 1) / NB);
-                    slot = atomicAdd(&S.hist[m], (1ULL << 32) | nb);
+                    slot = atomicAdd(&S.hist[m], (1u << 24) | nb);   // below 2^22 items, 128 polygons a group
                     sorted = true;
                 } else {
                     st_cand += (unsigned)n;    // an empty polygon: every candidate outside, bit 0
@@ -177,23 +177,24 @@ __global__ void __launch_bounds__(TP_THREADS) k_pip_tpp(ClassifyArgs a, LargeLis
             if (t == np - 1) S.c1 = ce;
         }
         __syncthreads();
-        // ---- exclusive scan of the histogram (warp 0; 9 keys per lane)
+        // ---- exclusive scan of the histogram (warp 0; 9 keys per lane); the two packed fields
+        //      never carry into each other
         if (t < 32) {
             constexpr int KPL = (TP_KEYS + 31) / 32;
-            unsigned long long loc[KPL], s = 0;
+            unsigned loc[KPL], s = 0;
             #pragma unroll
             for (int i = 0; i < KPL; ++i) {
                 const int key = KPL * lane + i;
-                loc[i] = key < TP_KEYS ? S.hist[key] : 0ULL;
+                loc[i] = key < TP_KEYS ? S.hist[key] : 0u;
                 s += loc[i];
             }
-            unsigned long long incl = s;
+            unsigned incl = s;
             #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
-                const unsigned long long v = __shfl_up_sync(FULL, incl, o);
+                const unsigned v = __shfl_up_sync(FULL, incl, o);
                 if (lane >= o) incl += v;
             }
-            unsigned long long run = incl - s;
+            unsigned run = incl - s;
             #pragma unroll
             for (int i = 0; i < KPL; ++i) {
                 const int key = KPL * lane + i;
@@ -201,8 +202,8 @@ __global__ void __launch_bounds__(TP_THREADS) k_pip_tpp(ClassifyArgs a, LargeLis
                 run += loc[i];
             }
             if (lane == 31) {
-                S.n_items = (int)(incl & 0xffffffffULL);
-                S.n_pos = (int)(incl >> 32);
+                S.n_items = (int)(incl & 0xffffffu);
+                S.n_pos = (int)(incl >> 24);
             }
         }
         __syncthreads();
@@ -211,10 +212,10 @@ __global__ void __launch_bounds__(TP_THREADS) k_pip_tpp(ClassifyArgs a, LargeLis
         const long long gnw = gc1 > gc0 ? (((long long)gc1 + 31) >> 5) - gw0 : 0;
         const bool staged = gnw <= TP_OB;
         if (sorted) {
-            const unsigned long long base = S.hist[m] + slot;   // no carry: items stay below 2^32
-            const int pos = (int)(base >> 32);
+            const unsigned base = S.hist[m] + slot;
+            const int pos = (int)(base >> 24);
             S.lp[pos] = (unsigned char)t;
-            S.start[pos] = (int)(base & 0xffffffffULL);
+            S.start[pos] = (int)(base & 0xffffffu);
         }
         if (t == 0) S.start[S.n_pos] = S.n_items;
         if (!staged)   // large and empty polygons' bits to 0 (k_pip_large XORs its parities in later)
@@ -223,7 +224,7 @@ __global__ void __launch_bounds__(TP_THREADS) k_pip_tpp(ClassifyArgs a, LargeLis
                 zero_bits(a.out_bits, (long long)__shfl_sync(FULL, cb, l), (long long)__shfl_sync(FULL, ce, l), lane);
             }
         __syncthreads();
-        for (int i = t; i < TP_KEYS; i += TP_THREADS) S.hist[i] = 0ULL;   // read for the last time above
+        for (int i = t; i < TP_KEYS; i += TP_THREADS) S.hist[i] = 0u;   // read for the last time above
         // ---- items in sorted order: item i is block (i - start[pos]) of the polygon at sorted
         //      position pos, start[pos] <= i < start[pos + 1]
         const int n_items = S.n_items, n_pos = S.n_pos;

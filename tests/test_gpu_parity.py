@@ -185,14 +185,20 @@ def test_footprints_scattered_points(api):
     check_full(api, W.scattered_points(W.footprints(seed=21, n_polys=20_000)))
 
 
-def test_filter_statistics(api):
-    """The device counters of the filtered kernel: every candidate is counted once, the box
-    rejects equal a numpy count of candidates outside their polygon's closed bounding box, and
-    the exact rechecks are a subset of the rest."""
+@pytest.mark.parametrize("kernel", [0, 1, 2], ids=["lockstep", "compacting", "thread-per-polygon"])
+def test_filter_statistics(api, kernel):
+    """The device counters of the filtered kernel, under each small-polygon kernel: every
+    candidate is counted once, the box rejects equal a numpy count of candidates outside their
+    polygon's closed bounding box, and the exact rechecks are a subset of the rest."""
     w = W.footprints(seed=5, n_polys=20_000)
-    api.pip_reset_stats()
-    gpu_bits(api, w)
-    s = api.pip_get_stats()
+    before = api.pip_get_small_tuning()
+    api.pip_set_small_tuning(kernel, 0, -1)
+    try:
+        api.pip_reset_stats()
+        gpu_bits(api, w)
+        s = api.pip_get_stats()
+    finally:
+        api.pip_set_small_tuning(*before)
     po, v, co, ids = w.poly_offsets.astype(np.int64), w.verts, w.cand_offsets.astype(np.int64), w.cand_ids
     owner = np.repeat(np.arange(len(po) - 1), np.diff(co))
     lo = np.stack([np.minimum.reduceat(v[:, k], po[:-1]) for k in (0, 1)], 1)
@@ -538,6 +544,30 @@ def test_verification_mode_finds_no_unsound_decision(api, name, make_w):
     assert s["verified_pairs"] > 0
     assert s["filter_errors"] == 0, f"{s['filter_errors']} of {s['verified_pairs']} trusted decisions were wrong"
     assert s["wait_timeouts"] == 0
+
+
+@pytest.mark.parametrize("kernel", [0, 1, 2], ids=["lockstep", "compacting", "thread-per-polygon"])
+def test_verification_mode_every_small_kernel(api, kernel):
+    """Verification mode under each small-polygon kernel, on the footprint batch and on the
+    int32-limit case (boxes at the corners of the int32 range against points anywhere in it, boxes
+    at the int32 test's bound).  For the thread-per-polygon kernel this checks its clamp edge by
+    edge: the int32 sign it computes on the clamped point must equal the exact sign on the raw
+    point for every straddling pair of an in-bound polygon."""
+    before = api.pip_get_small_tuning()
+    api.pip_set_small_tuning(kernel, 0, -1)
+    api.pip_set_verify(True)
+    try:
+        for w in (W.footprints(seed=9, n_polys=20_000), _extreme_small_case(np.random.default_rng(61))):
+            want = oracle.classify(w.points, w.poly_offsets, w.verts, w.cand_offsets, w.cand_ids)
+            api.pip_reset_stats()
+            got = gpu_bits(api, w)
+            s = api.pip_get_stats()
+            assert_same(got, want, w.n_bits, f"{w.name} kernel {kernel} (verification mode)")
+            assert s["verified_pairs"] > 0
+            assert s["filter_errors"] == 0, f"{w.name}: {s['filter_errors']} of {s['verified_pairs']} wrong"
+    finally:
+        api.pip_set_verify(False)
+        api.pip_set_small_tuning(*before)
 
 
 # ------------------------------------------------------------------------------------------
