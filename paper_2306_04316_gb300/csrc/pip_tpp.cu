@@ -65,6 +65,7 @@ __device__ __forceinline__ void put_bits(uint32_t *out, long long c, int n, unsi
 constexpr int TP_G = TP_THREADS;          // polygons of a group
 constexpr int TP_KEYS = WP_V + 1;         // sort keys: vertex counts 0..WP_V
 constexpr int TP_OB = 1024;               // output words staged per group
+constexpr int TP_ITAB = 1024;             // items whose sorted position is tabulated (else a binary search)
 
 template <typename CI>
 struct TppSmem {
@@ -75,7 +76,8 @@ struct TppSmem {
     int n[TP_G];                          // candidates
     int start[TP_G + 1];                  // first item at each sorted position (+ the total)
     unsigned char lp[TP_G];               // polygon (of the group) at each sorted position
-    alignas(16) unsigned out[TP_OB];      // staged output words (zeroed with 16-byte stores)
+    unsigned char ipos[TP_ITAB];          // sorted position of each item, when the group has at most TP_ITAB
+    alignas(16) unsigned out[2][TP_OB];   // staged output words, a buffer per group parity (zeroed with 16-byte stores)
     int n_items, n_pos;
     CI c0, c1;                            // candidate range of the group
 };
@@ -127,9 +129,12 @@ __global__ void __launch_bounds__(TP_THREADS) k_pip_tpp(ClassifyArgs a, LargeLis
     // after its last read (two barriers before the next group's counts)
     for (int i = t; i < TP_KEYS; i += TP_THREADS) S.hist[i] = 0u;
     __syncthreads();
-    for (int g = blockIdx.x; g < ngroups; g += gridDim.x) {
+    for (int g = blockIdx.x, it = 0; g < ngroups; g += gridDim.x, ++it) {
+        // the group's output words: the buffer the previous group did not use, so that this
+        // group's set-up does not wait for the previous group's writes
+        unsigned *const outw = S.out[it & 1];
         const int k0 = g * TP_G, np = min(TP_G, P - k0);
-        for (int i = t; i < TP_OB / 4; i += TP_THREADS) reinterpret_cast<uint4 *>(S.out)[i] = make_uint4(0, 0, 0, 0);
+        for (int i = t; i < TP_OB / 4; i += TP_THREADS) reinterpret_cast<uint4 *>(outw)[i] = make_uint4(0, 0, 0, 0);
         // ---- polygon k0 + t: offsets, large-polygon test, items, sort key
         int m = 0, n = 0;
         CI cb = 0, ce = 0;
@@ -213,9 +218,11 @@ __global__ void __launch_bounds__(TP_THREADS) k_pip_tpp(ClassifyArgs a, LargeLis
         const bool staged = gnw <= TP_OB;
         if (sorted) {
             const unsigned base = S.hist[m] + slot;
-            const int pos = (int)(base >> 24);
+            const int pos = (int)(base >> 24), first = (int)(base & 0xffffffu);
             S.lp[pos] = (unsigned char)t;
-            S.start[pos] = (int)(base & 0xffffffu);
+            S.start[pos] = first;
+            if (S.n_items <= TP_ITAB)   // each item's position, so that an item needs no search
+                for (int q = first, qe = first + (n + NB - 1) / NB; q < qe; ++q) S.ipos[q] = (unsigned char)pos;
         }
         if (t == 0) S.start[S.n_pos] = S.n_items;
         if (!staged)   // large and empty polygons' bits to 0 (k_pip_large XORs its parities in later)
@@ -229,10 +236,15 @@ __global__ void __launch_bounds__(TP_THREADS) k_pip_tpp(ClassifyArgs a, LargeLis
         //      position pos, start[pos] <= i < start[pos + 1]
         const int n_items = S.n_items, n_pos = S.n_pos;
         for (int i = t; i < n_items; i += TP_THREADS) {
-            int lo = 0, hi = n_pos;
-            while (hi - lo > 1) {
-                const int mid = (lo + hi) >> 1;
-                if (S.start[mid] <= i) lo = mid; else hi = mid;
+            int lo = 0;
+            if (n_items <= TP_ITAB) {
+                lo = S.ipos[i];
+            } else {
+                int hi = n_pos;
+                while (hi - lo > 1) {
+                    const int mid = (lo + hi) >> 1;
+                    if (S.start[mid] <= i) lo = mid; else hi = mid;
+                }
             }
             const int l = S.lp[lo];
             const int c0 = (i - S.start[lo]) * NB;
@@ -323,8 +335,8 @@ __global__ void __launch_bounds__(TP_THREADS) k_pip_tpp(ClassifyArgs a, LargeLis
                 const long long rel = pos0 - (gw0 << 5);
                 const long long wi = rel >> 5;
                 const int sh = (int)(rel & 31);
-                if (wi >= 0 && wi < gnw) atomicOr(&S.out[wi], bits << sh);
-                if (sh + nc > 32 && wi + 1 >= 0 && wi + 1 < gnw) atomicOr(&S.out[wi + 1], bits >> (32 - sh));
+                if (wi >= 0 && wi < gnw) atomicOr(&outw[wi], bits << sh);
+                if (sh + nc > 32 && wi + 1 >= 0 && wi + 1 < gnw) atomicOr(&outw[wi + 1], bits >> (32 - sh));
             } else {
                 put_bits(a.out_bits, pos0, nc, bits);
             }
@@ -335,9 +347,10 @@ __global__ void __launch_bounds__(TP_THREADS) k_pip_tpp(ClassifyArgs a, LargeLis
             for (long long w = t; w < gnw; w += TP_THREADS) {
                 const long long b0 = (gw0 + w) << 5;
                 const int lo = (int)max(0LL, (long long)gc0 - b0), hi = (int)min(32LL, (long long)gc1 - b0);
-                masked_store(a.out_bits + gw0 + w, range_mask(lo, hi), S.out[w]);
+                masked_store(a.out_bits + gw0 + w, range_mask(lo, hi), outw[w]);
             }
-        __syncthreads();   // S is rewritten by the next group
+        // no barrier here: the next group's set-up writes only the other output buffer and
+        // shared data that this group last read before its items barrier
     }
     if (a.stats) {
         #pragma unroll
