@@ -264,8 +264,9 @@ def pip_get_tuning():
 
 
 def pip_set_small_tuning(kernel=-1, slice=0, ctas_per_sm=-1):
-    """Small-polygon kernel: 1 = compacting, 0 = lockstep rounds; candidates per slice (128,
-    256); resident CTAs per SM (0 = as many as fit).  -1 / 0 keep a value."""
+    """Small-polygon kernel: 0 = lockstep rounds, 1 = compacting, 2 = thread per polygon;
+    candidates per slice (128, 256; kernel 2 takes slice / 16 per thread); resident CTAs per SM
+    (0 = as many as fit).  -1 / 0 keep a value."""
     _lib.check("pip_set_small_tuning", _lib.load().pip_set_small_tuning(kernel, slice, ctas_per_sm))
 
 
