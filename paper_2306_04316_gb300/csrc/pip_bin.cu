@@ -36,6 +36,7 @@ namespace pipdev {
 
 constexpr int BIN_CELL_CAP = 64;       // boxes covering more cells than this go on the short list
 constexpr int BIN_BIG_CAP = 256;       // most polygons on the short list
+constexpr int BIN_PACK_LEVEL = 16;     // cell edges up to 2^16: list boxes stored in 8 bytes, relative to the cell
 constexpr unsigned long long BIN_EMPTY = ~0ull;   // an empty hash slot (cx < 2^31 for level >= 1)
 constexpr int SCAN_TILE = 1024;        // elements per scan block (256 threads x 4)
 constexpr int SORT_LANE = 16;          // ids a lane sorts in its registers
@@ -254,6 +255,21 @@ __device__ __forceinline__ unsigned long long cell_key(unsigned cx, unsigned cy)
     return ((unsigned long long)cy << 32) | cx;
 }
 
+// A list box clipped to its cell (cx, cy) of edge 2^l <= 2^BIN_PACK_LEVEL, in coordinates relative
+// to the cell's corner: (x0 | x1 << 16, y0 | y1 << 16).  A point of that cell lies in the box
+// exactly when its own relative coordinates lie in the clipped one, so the probe's closed-box
+// test is unchanged while each list entry it reads takes 8 bytes instead of 16.
+__device__ __forceinline__ uint2 pack_box(int4 b, unsigned cx, unsigned cy, int l)
+{
+    const unsigned ox = cx << l, oy = cy << l, top = (1u << l) - 1u;
+    const unsigned bx0 = (unsigned)b.x ^ 0x80000000u, bx1 = (unsigned)b.z ^ 0x80000000u;
+    const unsigned by0 = (unsigned)b.y ^ 0x80000000u, by1 = (unsigned)b.w ^ 0x80000000u;
+    // the box covers the cell: bx0 <= ox + top and bx1 >= ox (likewise in y)
+    const unsigned x0 = bx0 > ox ? bx0 - ox : 0u, x1 = min(bx1 - ox, top);
+    const unsigned y0 = by0 > oy ? by0 - oy : 0u, y1 = min(by1 - oy, top);
+    return make_uint2(x0 | (x1 << 16), y0 | (y1 << 16));
+}
+
 __device__ __forceinline__ unsigned long long hash_slot(unsigned long long key, int hbits)
 {
     return (key * 0x9E3779B97F4A7C15ull) >> (64 - hbits);
@@ -353,7 +369,8 @@ __global__ void k_cells(const int4 *__restrict__ bb, const int32_t *__restrict__
                         }
                     } else if (ent[s].key == key) {
                         const unsigned j = atomicAdd(off + s, 1u);
-                        list_bb[j] = b;
+                        if (l <= BIN_PACK_LEVEL) reinterpret_cast<uint2 *>(list_bb)[j] = pack_box(b, cx, cy, l);
+                        else list_bb[j] = b;
                         list_id[j] = (int)k;
                         break;
                     }
@@ -393,9 +410,28 @@ __device__ __forceinline__ void probe_point(int2 p, long long i, int l, unsigned
         const int4 e = __ldg(reinterpret_cast<const int4 *>(ent + s));   // key, start, count
         const unsigned long long kk = ((unsigned long long)(unsigned)e.y << 32) | (unsigned)e.x;
         if (kk == key) {
-            for (int j = e.z; j < e.z + e.w; ++j) {
-                const int4 b = __ldg(list_bb + j);
-                if (p.x >= b.x && p.x <= b.z && p.y >= b.y && p.y <= b.w) emit(__ldg(list_id + j), i);
+            if (l <= BIN_PACK_LEVEL) {   // boxes clipped to the cell, relative to its corner
+                const unsigned lm = (1u << l) - 1u;
+                const unsigned rx = ((unsigned)p.x ^ 0x80000000u) & lm, ry = ((unsigned)p.y ^ 0x80000000u) & lm;
+                const uint2 *__restrict__ lb = reinterpret_cast<const uint2 *>(list_bb);
+                const int je = e.z + e.w;
+                // four boxes' loads in flight at a time (the loop would otherwise wait for each
+                // box before loading the next); a box past the run is empty (x0 > x1)
+                for (int j = e.z; j < je; j += 4) {
+                    uint2 b[4];
+                    #pragma unroll
+                    for (int u = 0; u < 4; ++u) b[u] = j + u < je ? __ldg(lb + j + u) : make_uint2(1u, 1u);
+                    #pragma unroll
+                    for (int u = 0; u < 4; ++u)
+                        if (rx >= (b[u].x & 0xffffu) && rx <= (b[u].x >> 16) && ry >= (b[u].y & 0xffffu) &&
+                            ry <= (b[u].y >> 16))
+                            emit(__ldg(list_id + j + u), i);
+                }
+            } else {
+                for (int j = e.z; j < e.z + e.w; ++j) {
+                    const int4 b = __ldg(list_bb + j);
+                    if (p.x >= b.x && p.x <= b.z && p.y >= b.y && p.y <= b.w) emit(__ldg(list_id + j), i);
+                }
             }
             break;
         }
