@@ -531,6 +531,52 @@ __device__ __forceinline__ void tile_parity_multi(const float4 *__restrict__ s_r
     }
 }
 
+// Parities of a thread's PPT candidates over a tile whose vertices span a box x0..x1, y0..y1 with
+// (W + 1)(H + 1) <= 2^30: every point is clamped to [x0 - 1, x1] x [y0 - 1, y1] first.  Each
+// edge's crossing of a horizontal line lies in [x0, x1], so a point left of the box has every
+// straddling edge's crossing strictly to its right before and after the clamp, a point at or right
+// of x1 none, and a point below y0 or at or above y1 straddles no edge: every edge's decision is
+// unchanged.  For the clamped point |det| <= (W + 1)|d_y| + (H + 1)|d_x| < 2 (W + 1)(H + 1) <=
+// 2^31, so the int32 record (c, a, b, y_j) of pip_edge.cuh evaluated with wrapping arithmetic gives
+// nt = -sign(d_y) det exactly, and the straddle test is the sign bit of (p_y - y_e) ^ (p_y - y_{e+1}):
+// no filter and no uncertainty.  All PPT candidates share each record load.
+template <int PPT, bool VERIFY>
+__device__ __forceinline__ void tile_parity_i32(const int4 *__restrict__ s_rec, const int2 *__restrict__ s_v,
+                                                int nt, const int2 (&p)[PPT], const bool (&ok)[PPT], int x0, int y0,
+                                                int x1, int y1, int (&par)[PPT], unsigned long long &n_err,
+                                                unsigned long long &n_ver)
+{
+    unsigned px[PPT], py[PPT], up[PPT], acc[PPT];
+    const unsigned yv0 = (unsigned)s_v[0].y;
+    #pragma unroll
+    for (int r = 0; r < PPT; ++r) {
+        px[r] = (unsigned)min(p[r].x < x0 ? x0 - 1 : p[r].x, x1);
+        py[r] = (unsigned)min(p[r].y < y0 ? y0 - 1 : p[r].y, y1);
+        up[r] = py[r] - yv0;
+        acc[r] = 0;
+    }
+    #pragma unroll 4
+    for (int e = 0; e < nt; ++e) {
+        const int4 q = s_rec[e];
+        #pragma unroll
+        for (int r = 0; r < PPT; ++r) {
+            const unsigned u = py[r] - (unsigned)q.w;
+            const unsigned x = u ^ up[r];
+            up[r] = u;
+            const unsigned ntv = (unsigned)q.x + px[r] * (unsigned)q.y + py[r] * (unsigned)q.z;
+            if (VERIFY && ok[r] && (int)x < 0) {   // a straddling edge: its exact test on the raw point
+                const int2 ri = s_v[e], rj = s_v[e + 1];
+                n_err += exact_edge_counts(p[r].x, p[r].y, ri.x, ri.y, rj.x, rj.y) != (int)(ntv >> 31);
+                ++n_ver;
+            }
+            acc[r] ^= x & ntv;
+        }
+    }
+    #pragma unroll
+    for (int r = 0; r < PPT; ++r)
+        if (ok[r]) par[r] ^= (int)(acc[r] >> 31);
+}
+
 // The same for a tile whose frame is below 2^30 from its centre, with scaled records: edge e is
 // (-c' s_e, |d_y| s_e, -s d_x s_e, y_{e+1}) with s_e = 2^-k_e >= 1 / (M_x |d_y| + M_y |d_x|), so
 // that nt = fma(P_y, ., fma(P_x, ., .)) = -s det s_e (rounded) and the edge's bound scaled by
@@ -644,6 +690,7 @@ __global__ void __launch_bounds__(LG_THREADS, PPT == 4 ? 3 : 4) k_pip_large(Clas
     __shared__ int s_item[4];          // polygon, candidate block, edge slice, valid
     __shared__ int s_pb[4], s_tb[4];
     __shared__ int s_tf[4];            // tile frame: ox, oy, bound (float bits), wide
+    __shared__ int s_vb[4];            // box of the tile's vertices alone
 
     constexpr int CB = LG_THREADS * PPT;
     const int tid = threadIdx.x, lane = tid & 31;
@@ -774,7 +821,10 @@ __global__ void __launch_bounds__(LG_THREADS, PPT == 4 ? 3 : 4) k_pip_large(Clas
                     if (ok[r]) par[r] ^= global_exact_parity(a.verts + base, m, e0, e0 + nt, pt[r]);
                 continue;
             }
-            if (tid == 0) { s_tb[0] = s_pb[0]; s_tb[1] = s_pb[1]; s_tb[2] = s_pb[2]; s_tb[3] = s_pb[3]; }
+            if (tid == 0) {
+                s_tb[0] = s_pb[0]; s_tb[1] = s_pb[1]; s_tb[2] = s_pb[2]; s_tb[3] = s_pb[3];
+                s_vb[0] = INT_MAX; s_vb[1] = INT_MAX; s_vb[2] = INT_MIN; s_vb[3] = INT_MIN;
+            }
             // the tile's vertices e0 .. e0 + nt (the last one is vertex 0 when the tile closes the
             // polygon): the 16-byte-aligned interior of the contiguous run by one bulk copy, the
             // at most one vertex before and after it and the closing vertex by plain loads
@@ -817,6 +867,7 @@ __global__ void __launch_bounds__(LG_THREADS, PPT == 4 ? 3 : 4) k_pip_large(Clas
             }
             if (lane == 0) {
                 atomicMin(&s_tb[0], x0); atomicMin(&s_tb[1], y0); atomicMax(&s_tb[2], x1); atomicMax(&s_tb[3], y1);
+                atomicMin(&s_vb[0], x0); atomicMin(&s_vb[1], y0); atomicMax(&s_vb[2], x1); atomicMax(&s_vb[3], y1);
             }
             __syncthreads();
             if (tid == 0) {
@@ -833,8 +884,19 @@ __global__ void __launch_bounds__(LG_THREADS, PPT == 4 ? 3 : 4) k_pip_large(Clas
             const unsigned Mx = (unsigned)s_tf[2], My = (unsigned)s_tf[3];
             const bool wide = (Mx >= (1u << 30)) | (My >= (1u << 30));
             const float fMx = __uint2float_ru(Mx), fMy = __uint2float_ru(My);
+            // a tile whose own vertices span a box with (W + 1)(H + 1) <= 2^30 takes the exact int32
+            // test on points clamped to [x0 - 1, x1] x [y0 - 1, y1] of that box (each edge's
+            // decision unchanged), whatever the spread of the block's points
+            const int vx0 = s_vb[0], vy0 = s_vb[1], vx1 = s_vb[2], vy1 = s_vb[3];
+            const unsigned VW = (unsigned)vx1 - (unsigned)vx0, VH = (unsigned)vy1 - (unsigned)vy0;
+            const bool i32 = VW < (1u << 30) && VH < (1u << 30) && (VW + 1ULL) * (VH + 1ULL) <= (1ULL << 30);
             for (int i = tid; i < nt; i += LG_THREADS) {
                 const int2 ri = s_v[i], rj = s_v[i + 1];
+                if (i32) {
+                    const int4 r4 = int32_record(ri, rj);
+                    reinterpret_cast<int4 *>(s_rec)[i] = r4;
+                    continue;
+                }
                 const long long ady = llabs((long long)rj.y - ri.y), adx = llabs((long long)rj.x - ri.x);
                 // M_x |d_y| + M_y |d_x|, rounded up
                 const float S = __fadd_ru(__fmul_ru(fMx, __ll2float_ru(ady)), __fmul_ru(fMy, __ll2float_ru(adx)));
@@ -856,7 +918,10 @@ __global__ void __launch_bounds__(LG_THREADS, PPT == 4 ? 3 : 4) k_pip_large(Clas
                 s_rec[i] = rec;
             }
             __syncthreads();
-            if (!wide)
+            if (i32)
+                tile_parity_i32<PPT, VERIFY>(reinterpret_cast<const int4 *>(s_rec), s_v, nt, pt, ok, vx0, vy0, vx1, vy1,
+                                             par, st_err, st_ver);
+            else if (!wide)
                 tile_parity_scaled<PPT, VERIFY>(reinterpret_cast<const int4 *>(s_rec), s_v, nt, pt, ok, ox, oy, par,
                                                 st_fbp, st_err, st_ver);
             else
