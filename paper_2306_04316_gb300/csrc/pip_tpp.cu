@@ -20,10 +20,10 @@
 // or above y1 has no straddling edge before or after; a point left of x0 (right of x1) is left
 // (right) of every crossing of its ray before and after, so every (no) straddling edge counts.
 // For a clamped point |det| <= (W + 1)|d_y| + (H + 1)|d_x| < 2 (W + 1)(H + 1), so when
-// (W + 1)(H + 1) < 2^30 the wrapping 32-bit evaluation gives -sign(d_y) det exactly.  Polygons
-// outside that bound (boxes of 2^30 or more) take the exact 64/128-bit test edge by edge in the
-// same thread: correct, but slow, so the autotuner keeps the other small-polygon kernels for
-// batches of such polygons.
+// (W + 1)(H + 1) < 2^30 the wrapping 32-bit evaluation gives -sign(d_y) det exactly.  Boxes below
+// 2^31 on both sides take the same walk with exact int64 products in the frame of the box's
+// corner, and boxes of 2^31 or more the exact 64/128-bit test edge by edge in the same thread:
+// correct, but slow, so the autotuner keeps the lockstep kernel for batches with many of those.
 //
 // Polygons with more than 256 vertices or more than 2^18 (candidate, edge) pairs go on the
 // large-polygon list and get bit 0 here, as in the other small-polygon kernels.  Each thread
@@ -322,6 +322,48 @@ __global__ void __launch_bounds__(TP_THREADS) k_pip_tpp(ClassifyArgs a, LargeLis
                         if (CARRY) u[CARRY ? j : 0] = uj;
                     }
                     ri = rj;
+                }
+                #pragma unroll
+                for (int j = 0; j < NB; ++j) bits |= (acc[j] >> 31) << j;
+            } else if (W < 0x7fffffffu && H < 0x7fffffffu) {
+                // boxes below 2^31: the same clamp, then the exact test in int64 in the frame of the
+                // box's corner (x0, y0): every clamped difference fits in 32 bits, so
+                // nt = (P_x - X_i)|d_y| + (P_y - Y_i)(-s d_x) = -sign(d_y) det takes two 32 x 32 -> 64
+                // multiply-adds; the straddle test is the sign bit of (P_y - Y_i) ^ (P_y - Y_j)
+                int fx[NB], fy[NB];
+                #pragma unroll
+                for (int j = 0; j < NB; ++j) {
+                    fx[j] = (int)((unsigned)min(px[j] < x0 ? x0 - 1 : px[j], x1) - (unsigned)x0);
+                    fy[j] = (int)((unsigned)min(py[j] < y0 ? y0 - 1 : py[j], y1) - (unsigned)y0);
+                }
+                int2 ri = __ldg(V + mv - 1);
+                int ri_x = (int)((unsigned)ri.x - (unsigned)x0), ri_y = (int)((unsigned)ri.y - (unsigned)y0);
+                int u[NB];
+                unsigned acc[NB];
+                #pragma unroll
+                for (int j = 0; j < NB; ++j) {
+                    u[j] = fy[j] - ri_y;
+                    acc[j] = 0;
+                }
+                for (int e = 0; e < mv; ++e) {
+                    const int2 rj = __ldg(V + e);
+                    const int rj_x = (int)((unsigned)rj.x - (unsigned)x0), rj_y = (int)((unsigned)rj.y - (unsigned)y0);
+                    const int dx = rj_x - ri_x, dy = rj_y - ri_y;   // |d_x| <= W, |d_y| <= H: no overflow
+                    const int ady = dy > 0 ? dy : -dy, nsdx = dy > 0 ? -dx : dx;
+                    #pragma unroll
+                    for (int j = 0; j < NB; ++j) {
+                        const int uj = fy[j] - rj_y;
+                        const long long nt = (long long)(fx[j] - ri_x) * ady + (long long)u[j] * nsdx;
+                        if (VERIFY && ((valid >> j) & 1u) && (u[j] ^ uj) < 0) {
+                            st_err += exact_edge_counts(px[j], py[j], ri.x, ri.y, rj.x, rj.y) != (int)(nt < 0);
+                            ++st_ver;
+                        }
+                        acc[j] ^= (unsigned)(u[j] ^ uj) & (unsigned)((unsigned long long)nt >> 32);
+                        u[j] = uj;
+                    }
+                    ri = rj;
+                    ri_x = rj_x;
+                    ri_y = rj_y;
                 }
                 #pragma unroll
                 for (int j = 0; j < NB; ++j) bits |= (acc[j] >> 31) << j;
