@@ -40,7 +40,8 @@ constexpr int BIN_PACK_LEVEL = 16;     // cell edges up to 2^16: list boxes stor
 constexpr unsigned long long BIN_EMPTY = ~0ull;   // an empty hash slot (cx < 2^31 for level >= 1)
 constexpr int SCAN_TILE = 1024;        // elements per scan block (256 threads x 4)
 constexpr int SORT_LANE = 16;          // ids a lane sorts in its registers
-constexpr int SORT_WARP_SMEM = 1024;   // ids a warp sorts in its own shared memory
+constexpr int SORT_WARP_REG = 4;       // ids a lane holds when a warp sorts a list in registers (128 a warp)
+constexpr int SORT_WARP_SMEM = 512;    // ids a warp sorts in its own shared memory
 constexpr int SORT_CTA_SMEM = 8192;    // ids a CTA sorts in shared memory
 
 constexpr unsigned INDEX_MAGIC = 0x50495849u;   // a polygon index whose build has completed
@@ -536,21 +537,63 @@ __global__ void __launch_bounds__(PROBE_THREADS, 8) k_probe_fill(
 // ------------------------------------------------------------------------------------------
 // per polygon: its ids sorted ascending
 // ------------------------------------------------------------------------------------------
-// 32 values, one per lane, sorted ascending across the warp (bitonic network whose comparators
-// all put the smaller value at the lower lane).
-__device__ __forceinline__ int warp_sort32(int v, int lane)
+// 32 K values, value r * 32 + lane in register v[r] of the lane, sorted ascending across the warp
+// in the same layout.  Bitonic network whose comparators all put the smaller value at the lower
+// position: each stage of block size kk starts by comparing position p with its mirror
+// p ^ (kk - 1), then p with p ^ j for j = kk / 4 .. 1.  A partner in another lane comes by a
+// shuffle; one in another register of the same lane (j >= 32) is compared in place.
+template <int K>
+__device__ __forceinline__ void warp_sort_regs(int (&v)[K], int lane)
 {
     #pragma unroll
-    for (int kk = 2; kk <= 32; kk <<= 1) {
-        int o = __shfl_xor_sync(FULL, v, kk - 1);                  // mirror within blocks of kk
-        v = (lane & (kk - 1)) < (kk >> 1) ? min(v, o) : max(v, o);
+    for (int kk = 2; kk <= 32 * K; kk <<= 1) {
+        if (kk <= 32) {
+            #pragma unroll
+            for (int r = 0; r < K; ++r) {
+                const int o = __shfl_xor_sync(FULL, v[r], kk - 1);
+                v[r] = (lane & (kk >> 1)) ? max(v[r], o) : min(v[r], o);
+            }
+        } else {
+            // mirror of (r, lane) is (r ^ (kk / 32 - 1), lane ^ 31); the lower one of the pair is
+            // the one whose register has bit kk / 64 clear
+            int o[K];
+            #pragma unroll
+            for (int r = 0; r < K; ++r) o[r] = __shfl_xor_sync(FULL, v[r ^ (kk / 32 - 1)], 31);
+            #pragma unroll
+            for (int r = 0; r < K; ++r) v[r] = (r & (kk / 64)) ? max(v[r], o[r]) : min(v[r], o[r]);
+        }
         #pragma unroll
         for (int j = kk >> 2; j > 0; j >>= 1) {
-            o = __shfl_xor_sync(FULL, v, j);
-            v = (lane & j) ? max(v, o) : min(v, o);
+            if (j >= 32) {
+                #pragma unroll
+                for (int r = 0; r < K; ++r)
+                    if (!(r & (j / 32))) {
+                        const int x = v[r], y = v[r | (j / 32)];
+                        v[r] = min(x, y);
+                        v[r | (j / 32)] = max(x, y);
+                    }
+            } else {
+                #pragma unroll
+                for (int r = 0; r < K; ++r) {
+                    const int o = __shfl_xor_sync(FULL, v[r], j);
+                    v[r] = (lane & j) ? max(v[r], o) : min(v[r], o);
+                }
+            }
         }
     }
-    return v;
+}
+
+// A list of n <= 32 K ids at ids[a ..) sorted by one warp in registers.
+template <int K>
+__device__ __forceinline__ void warp_sort_list(int32_t *ids, long long a, long long n, int lane)
+{
+    int v[K];
+    #pragma unroll
+    for (int r = 0; r < K; ++r) v[r] = r * 32 + lane < n ? ids[a + r * 32 + lane] : INT_MAX;
+    warp_sort_regs<K>(v, lane);
+    #pragma unroll
+    for (int r = 0; r < K; ++r)
+        if (r * 32 + lane < n) ids[a + r * 32 + lane] = v[r];
 }
 
 // V[0..n) sorted ascending by threads t0, t0 + nt, ... of a group that `sync` synchronises: the
@@ -637,8 +680,8 @@ __global__ void __launch_bounds__(256) k_seg_sort(const int32_t *__restrict__ ca
     }
 }
 
-// The queued lists of up to SORT_WARP_SMEM ids, one warp each: in registers up to 32, else in
-// the warp's shared memory.
+// The queued lists of up to SORT_WARP_SMEM ids, one warp each: in registers up to
+// 32 SORT_WARP_REG ids, else in the warp's shared memory.
 __global__ void __launch_bounds__(256) k_seg_sort_medium(const int32_t *__restrict__ cand_offsets, int32_t *ids,
                                                          long long capacity, const ProbeHeader *h,
                                                          const int *medium_list)
@@ -654,9 +697,11 @@ __global__ void __launch_bounds__(256) k_seg_sort_medium(const int32_t *__restri
         const long long a = min((long long)cand_offsets[k], capacity);
         const long long n = min((long long)cand_offsets[k + 1], capacity) - a;
         if (n <= 32) {
-            int v = lane < n ? ids[a + lane] : INT_MAX;
-            v = warp_sort32(v, lane);
-            if (lane < n) ids[a + lane] = v;
+            warp_sort_list<1>(ids, a, n, lane);
+        } else if (n <= 64) {
+            warp_sort_list<2>(ids, a, n, lane);
+        } else if (n <= 32 * SORT_WARP_REG) {
+            warp_sort_list<SORT_WARP_REG>(ids, a, n, lane);
         } else {
             for (int i = lane; i < n; i += 32) wv[i] = ids[a + i];
             __syncwarp();

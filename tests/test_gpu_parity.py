@@ -276,8 +276,9 @@ def test_out_of_range_ids_read_nothing(api, exact):
 
 def _bin_case(rng):
     """Polygons that exercise every path of the binning: tiny boxes, boxes large enough to go on
-    the short list, empty polygons, and id lists long enough for each sort (warp registers,
-    warp shared memory, CTA shared memory, global memory)."""
+    the short list, empty polygons, and id lists long enough for each sort (a lane's registers,
+    a warp's registers at 1, 2 and 4 ids a lane, warp shared memory, CTA shared memory, global
+    memory)."""
     polys = []
     for _ in range(300):                      # tiny squares (a few points each)
         x, y = rng.integers(-10**6, 10**6, 2)
@@ -285,6 +286,9 @@ def _bin_case(rng):
         polys.append(np.array([[x, y], [x + s, y], [x + s, y + s], [x, y + s]], dtype=np.int64))
     hot = rng.integers(-10**6 + 50_000, 10**6 - 50_000, (2, 2))          # two hot spots of points
     for (x, y), s in zip(hot, (3000, 16000)):                            # ~10^2 and ~10^3 points
+        polys.append(np.array([[x, y], [x + s, y], [x, y + s]], dtype=np.int64))
+    x, y = hot[0] - 19_000                    # lists of about 20, 50, 100, 400 and 850 ids
+    for s in (1500, 2300, 3300, 6500, 9500):
         polys.append(np.array([[x, y], [x + s, y], [x, y + s]], dtype=np.int64))
     polys.append(np.zeros((0, 2), dtype=np.int64))                      # empty polygon
     big = 2 * 10**6
@@ -313,8 +317,9 @@ def test_binning_paths_and_cell_sizes(api, cell_size):
     co, ids = api.bin_join(d_pts, d_po, d_v, cell_size=cell_size)
     torch.cuda.synchronize()
     counts, want_ids = oracle.bbox_join(pts, po, verts, np.arange(P))
-    assert counts.max() > 8192 and ((counts > 1024) & (counts <= 8192)).any()
-    assert ((counts > 32) & (counts <= 1024)).any()
+    assert counts.max() > 8192
+    for lo, hi in ((1, 16), (16, 32), (32, 64), (64, 128), (128, 512), (512, 8192)):
+        assert ((counts > lo) & (counts <= hi)).any(), (lo, hi)
     assert np.array_equal(np.diff(co.cpu().numpy().astype(np.int64)), counts)
     assert np.array_equal(ids.cpu().numpy(), want_ids)
 
