@@ -154,4 +154,16 @@ __device__ __forceinline__ float4 fp32_record(int2 ri, int2 rj, int ox, int oy)
     return dy > 0 ? make_float4(c, fdy, fdx, __int_as_float(rj.y)) : make_float4(-c, -fdy, -fdx, __int_as_float(rj.y));
 }
 
+// The same FP32 record from int64 differences, for frames of 2^31 or more (where the int32
+// differences of fp32_record would wrap): the four inputs are rounded from exact integers as in
+// fp32_record, so the same bound holds.  (c, a, b) = s (X d_y - Y d_x), |d_y|, s d_x.
+__device__ __forceinline__ float3 fp32_record_ll(int2 ri, int2 rj, int ox, int oy)
+{
+    const long long dx = (long long)rj.x - ri.x, dy = (long long)rj.y - ri.y;
+    const float fdx = __ll2float_rn(dx), fdy = __ll2float_rn(dy);
+    const float X = __ll2float_rn((long long)ri.x - ox), Y = __ll2float_rn((long long)ri.y - oy);
+    const float c = __fmaf_rn(X, fdy, -__fmul_rn(Y, fdx));
+    return dy > 0 ? make_float3(c, fdy, fdx) : make_float3(-c, -fdy, -fdx);
+}
+
 }  // namespace pipdev

@@ -118,7 +118,7 @@ __global__ void __launch_bounds__(TP_THREADS) k_pip_tpp(ClassifyArgs a, LargeLis
     const long long NPTS = a.n_points;
     const CI W32 = (CI)(a.words_per_poly * 32);
     const int ngroups = (P + TP_G - 1) / TP_G;
-    unsigned st_cand = 0, st_in = 0, st_err = 0, st_ver = 0;
+    unsigned st_cand = 0, st_in = 0, st_err = 0, st_ver = 0, st_fb = 0;
     if (!DENSE && blockIdx.x == 0 && t == 0 && P > 0) {
         // bits past the last candidate in the final word are 0
         const long long C = __ldg(a.cand_offsets + P);
@@ -367,8 +367,61 @@ __global__ void __launch_bounds__(TP_THREADS) k_pip_tpp(ClassifyArgs a, LargeLis
                 }
                 #pragma unroll
                 for (int j = 0; j < NB; ++j) bits |= (acc[j] >> 31) << j;
-            } else {
+            } else if (NB > 8) {
+                // (16-candidate blocks keep their registers for the int32 walk)
                 bits = tpp_exact_block<DENSE>(a, V, mv, (long long)cbv, c0, nc);
+            } else {
+                // boxes of 2^31 or more on a side: the FP32 filter in the frame of the box's centre
+                // (records from int64 differences) with the forward-error bound 13u (M_x H + M_y W)
+                // of pip_edge.cuh, valid for points in the closed box; a point outside it has
+                // parity 0 (masked below), and a candidate whose sign came within the bound on a
+                // straddling edge is decided exactly
+                const unsigned Mx = W - (W >> 1), My = H - (H >> 1);
+                const int ox = x0 + (int)(W >> 1), oy = y0 + (int)(H >> 1);
+                const float B = __fmul_ru(PM_BOUND_K, __fadd_ru(__fmul_ru(__uint2float_ru(Mx), __uint2float_ru(H)),
+                                                                __fmul_ru(__uint2float_ru(My), __uint2float_ru(W))));
+                float fx[NB], fy[NB];
+                #pragma unroll
+                for (int j = 0; j < NB; ++j) {
+                    const bool in = (inm >> j) & 1u;
+                    fx[j] = in ? __ll2float_rn((long long)px[j] - ox) : 0.f;
+                    fy[j] = in ? __ll2float_rn((long long)py[j] - oy) : 0.f;
+                }
+                int2 ri = __ldg(V + mv - 1);
+                unsigned sp = 0, par = 0, unc = 0;   // per candidate: y_i > p_y, parity, uncertain
+                #pragma unroll
+                for (int j = 0; j < NB; ++j) sp |= (unsigned)(ri.y > py[j]) << j;
+                for (int e = 0; e < mv; ++e) {
+                    const int2 rj = __ldg(V + e);
+                    const float3 r = fp32_record_ll(ri, rj, ox, oy);
+                    unsigned sn = 0;
+                    #pragma unroll
+                    for (int j = 0; j < NB; ++j) sn |= (unsigned)(rj.y > py[j]) << j;
+                    const unsigned st = sn ^ sp;   // straddling edges
+                    sp = sn;
+                    unsigned pos = 0, near = 0;
+                    #pragma unroll
+                    for (int j = 0; j < NB; ++j) {
+                        // tt = det (d_y > 0) or -det (d_y < 0): a straddling edge counts when tt > 0
+                        const float tt = __fmaf_rn(fy[j], r.z, __fmaf_rn(-fx[j], r.y, r.x));
+                        pos |= (unsigned)(tt > 0.f) << j;
+                        near |= (unsigned)(fabsf(tt) <= B) << j;
+                        if (VERIFY && ((inm & st) >> j & 1u) && !(fabsf(tt) <= B)) {
+                            st_err += exact_edge_counts(px[j], py[j], ri.x, ri.y, rj.x, rj.y) != (int)(tt > 0.f);
+                            ++st_ver;
+                        }
+                    }
+                    par ^= pos & st;
+                    unc |= near & st;
+                    ri = rj;
+                }
+                bits = par & inm;
+                unc &= inm;
+                st_fb += __popc(unc);
+                for (unsigned q = unc; q; q &= q - 1) {
+                    const int j = __ffs(q) - 1;
+                    bits = (bits & ~(1u << j)) | (tpp_exact_block<DENSE>(a, V, mv, (long long)cbv, c0 + j, 1) << j);
+                }
             }
             bits &= valid;
             // ---- the item's bits
@@ -399,6 +452,7 @@ __global__ void __launch_bounds__(TP_THREADS) k_pip_tpp(ClassifyArgs a, LargeLis
         for (int o = 16; o > 0; o >>= 1) {
             st_cand += __shfl_down_sync(FULL, st_cand, o);
             st_in += __shfl_down_sync(FULL, st_in, o);
+            st_fb += __shfl_down_sync(FULL, st_fb, o);
             if (VERIFY) st_err += __shfl_down_sync(FULL, st_err, o);
             if (VERIFY) st_ver += __shfl_down_sync(FULL, st_ver, o);
         }
@@ -407,6 +461,7 @@ __global__ void __launch_bounds__(TP_THREADS) k_pip_tpp(ClassifyArgs a, LargeLis
             if (VERIFY && st_ver) atomicAdd(a.stats + ST_VERIFIED, (unsigned long long)st_ver);
             if (st_cand) atomicAdd(a.stats + ST_CANDIDATES, (unsigned long long)st_cand);
             if (st_rej) atomicAdd(a.stats + ST_BBOX_REJECTS, (unsigned long long)st_rej);
+            if (st_fb) atomicAdd(a.stats + ST_FALLBACK_POINTS, (unsigned long long)st_fb);
             if (VERIFY && st_err) atomicAdd(a.stats + ST_FILTER_ERRORS, (unsigned long long)st_err);
         }
     }
