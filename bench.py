@@ -649,7 +649,7 @@ def other_configs(args, peaks, peak_kind, n_sm):
     res = {}
     stream = torch.cuda.Stream()
     small0, large0 = api.pip_get_small_tuning(), api.pip_get_tuning()
-    large_grid = [(2048, 4, 3), (4096, 4, 3), (4096, 4, 2)]
+    large_grid = [(256, 4, 3), (512, 4, 3), (2048, 4, 3), (4096, 4, 2)]
     for name, steps in (("star", 20), ("stress", 20), ("fractal", 4), ("country", 3)):
         w = make_workload(name, 0, 1.0)
         T, B = w.pair_tests(), w.algorithmic_bytes()

@@ -14,7 +14,7 @@ import json
 import math
 import os
 
-DEFAULT_GRID = [(t, p, c) for t in (1024, 2048, 4096) for p in (1, 2, 4) for c in (2, 3, 4)]
+DEFAULT_GRID = [(t, p, c) for t in (256, 512, 1024, 2048, 4096) for p in (1, 2, 4) for c in (2, 3, 4)]
 # small-polygon kernel: (kernel: 0 lockstep / 1 compacting / 2 thread per polygon, candidates per slice
 # (kernel 2: slice / 16 per thread), CTAs per SM, 0 = all)
 SMALL_GRID = [(0, 256, 0), (0, 128, 0), (0, 256, 4), (1, 256, 0), (1, 128, 0), (1, 256, 3), (2, 256, 0),

@@ -5,7 +5,8 @@ configuration that bench.py times; every bit is compared with the oracle (0 mism
   (test_gpu_parity.test_star_full), the fractal batch (64 polygons of 1e4-1e6 vertices, 10M
   points, about 8e11 pair tests) and the paper-shaped country batch (17,097,823 points against
   one 100,000-vertex polygon, dense): all bits, both kernels;
-- footprints and stress again under every small-polygon kernel shape of the autotuner's grid;
+- footprints and stress again under every small-polygon kernel shape of the autotuner's grid,
+  fractal and country under every edge tile the bench may pick;
 - the spatial join (100k polygons against one full 10M-point batch): the GPU candidate lists
   must equal the closed-box lists computed here from the definition on points sorted by x
   (that computation is itself checked against the oracle's brute-force join on 100 polygons),
@@ -50,12 +51,22 @@ def test_full_size_every_small_kernel(api, make):
         api.pip_set_small_tuning(*before)
 
 
-def test_fractal_full_size(api):
-    check_full(api, W.fractal(), "full size")
-
-
-def test_country_full_size(api):
-    check_full(api, W.country(), "full size")
+@pytest.mark.parametrize("make", [W.fractal, W.country], ids=["fractal", "country"])
+def test_large_polygons_full_size(api, make):
+    """Every bit of the fractal and country batches, both kernels at the default tuning, and the
+    filtered kernel again at every edge tile the bench's autotuner may pick for them (the smaller
+    the tile, the more tiles take the exact int32 test instead of the FP32 filter)."""
+    w = make()
+    want = oracle.classify(w.points, w.poly_offsets, w.verts, w.cand_offsets, w.cand_ids)
+    for exact in (False, True):
+        assert_same(gpu_bits(api, w, exact), want, w.n_bits, f"{w.name} full size {'exact' if exact else 'filtered'}")
+    before = api.pip_get_tuning()
+    try:
+        for t in ((256, 4, 3), (512, 4, 3), (4096, 4, 2)):
+            api.pip_set_tuning(*t)
+            assert_same(gpu_bits(api, w), want, w.n_bits, f"{w.name} full size tuning={t}")
+    finally:
+        api.pip_set_tuning(*before)
 
 
 def _closed_box_lists(points, poly_offsets, verts):
