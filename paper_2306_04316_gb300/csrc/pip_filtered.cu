@@ -540,19 +540,27 @@ __device__ __forceinline__ void tile_parity_multi(const float4 *__restrict__ s_r
 // 2^31, so the int32 record (c, a, b, y_j) of pip_edge.cuh evaluated with wrapping arithmetic gives
 // nt = -sign(d_y) det exactly, and the straddle test is the sign bit of (p_y - y_e) ^ (p_y - y_{e+1}):
 // no filter and no uncertainty.  All PPT candidates share each record load.
-template <int PPT, bool VERIFY>
+// FY (a tile less than 2^24 high): the records hold y_{e+1} - y0 as an FP32 number and the
+// straddle subtraction runs in FP32 on the clamped p_y - y0; both operands and their difference
+// are integers of magnitude at most 2^24, so it is exact, and an exact zero is +0 (sign bit clear,
+// as for the integer difference).  That moves one of the three integer-pipe operations of a pair
+// to the FMA pipe, which the pair's two multiply-adds share with it.
+template <int PPT, bool VERIFY, bool FY>
 __device__ __forceinline__ void tile_parity_i32(const int4 *__restrict__ s_rec, const int2 *__restrict__ s_v,
                                                 int nt, const int2 (&p)[PPT], const bool (&ok)[PPT], int x0, int y0,
                                                 int x1, int y1, int (&par)[PPT], unsigned long long &n_err,
                                                 unsigned long long &n_ver)
 {
     unsigned px[PPT], py[PPT], up[PPT], acc[PPT];
+    float fpy[PPT];
     const unsigned yv0 = (unsigned)s_v[0].y;
+    const float fyv0 = __int2float_rn(s_v[0].y - y0);
     #pragma unroll
     for (int r = 0; r < PPT; ++r) {
         px[r] = (unsigned)min(p[r].x < x0 ? x0 - 1 : p[r].x, x1);
         py[r] = (unsigned)min(p[r].y < y0 ? y0 - 1 : p[r].y, y1);
-        up[r] = py[r] - yv0;
+        fpy[r] = __int2float_rn((int)(py[r] - (unsigned)y0));
+        up[r] = FY ? __float_as_uint(__fsub_rn(fpy[r], fyv0)) : py[r] - yv0;
         acc[r] = 0;
     }
     #pragma unroll 4
@@ -560,7 +568,7 @@ __device__ __forceinline__ void tile_parity_i32(const int4 *__restrict__ s_rec, 
         const int4 q = s_rec[e];
         #pragma unroll
         for (int r = 0; r < PPT; ++r) {
-            const unsigned u = py[r] - (unsigned)q.w;
+            const unsigned u = FY ? __float_as_uint(__fsub_rn(fpy[r], __int_as_float(q.w))) : py[r] - (unsigned)q.w;
             const unsigned x = u ^ up[r];
             up[r] = u;
             const unsigned ntv = (unsigned)q.x + px[r] * (unsigned)q.y + py[r] * (unsigned)q.z;
@@ -890,10 +898,12 @@ __global__ void __launch_bounds__(LG_THREADS, PPT == 4 ? 3 : 4) k_pip_large(Clas
             const int vx0 = s_vb[0], vy0 = s_vb[1], vx1 = s_vb[2], vy1 = s_vb[3];
             const unsigned VW = (unsigned)vx1 - (unsigned)vx0, VH = (unsigned)vy1 - (unsigned)vy0;
             const bool i32 = VW < (1u << 30) && VH < (1u << 30) && (VW + 1ULL) * (VH + 1ULL) <= (1ULL << 30);
+            const bool fy = i32 && VH < (1u << 24);   // the straddle subtraction in FP32 (exact)
             for (int i = tid; i < nt; i += LG_THREADS) {
                 const int2 ri = s_v[i], rj = s_v[i + 1];
                 if (i32) {
-                    const int4 r4 = int32_record(ri, rj);
+                    int4 r4 = int32_record(ri, rj);
+                    if (fy) r4.w = __float_as_int(__int2float_rn(rj.y - vy0));
                     reinterpret_cast<int4 *>(s_rec)[i] = r4;
                     continue;
                 }
@@ -918,9 +928,12 @@ __global__ void __launch_bounds__(LG_THREADS, PPT == 4 ? 3 : 4) k_pip_large(Clas
                 s_rec[i] = rec;
             }
             __syncthreads();
-            if (i32)
-                tile_parity_i32<PPT, VERIFY>(reinterpret_cast<const int4 *>(s_rec), s_v, nt, pt, ok, vx0, vy0, vx1, vy1,
-                                             par, st_err, st_ver);
+            if (fy)
+                tile_parity_i32<PPT, VERIFY, true>(reinterpret_cast<const int4 *>(s_rec), s_v, nt, pt, ok, vx0, vy0, vx1,
+                                                   vy1, par, st_err, st_ver);
+            else if (i32)
+                tile_parity_i32<PPT, VERIFY, false>(reinterpret_cast<const int4 *>(s_rec), s_v, nt, pt, ok, vx0, vy0, vx1,
+                                                    vy1, par, st_err, st_ver);
             else if (!wide)
                 tile_parity_scaled<PPT, VERIFY>(reinterpret_cast<const int4 *>(s_rec), s_v, nt, pt, ok, ox, oy, par,
                                                 st_fbp, st_err, st_ver);
