@@ -402,6 +402,30 @@ def run_join(args, rank, world, quiet=False):
     best, times = tuning.autotune(d_pts[0], d_po, d_v, co[0], ids[0], n_cands=totals[0], cache=False)
     autotuned = {"best": list(best), "candidates": len(times), "best_ms": times[best],
                  "small": {"best": list(best_s), "candidates": len(times_s), "best_ms": times_s[best_s]}}
+    # The large-polygon kernel's tuning also sets how much of each SM its CTAs hold while they wait
+    # for the small-polygon kernel before them (programmatic dependent launch); with four streams
+    # overlapping, that matters more than the single-call times above, which are all within noise
+    # here.  So a few tunings (the single-call pick and one per edge tile) are timed on the step.
+    step_ms = {}
+    for t in [tuple(best)] + [t for t in ((256, 4, 3), (512, 2, 2), (1024, 4, 3), (2048, 4, 3)) if t != tuple(best)]:
+        api.pip_set_tuning(*t)
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=stream):
+            one_pass(True)
+        with torch.cuda.stream(stream):
+            g.replay()
+            stream.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(3):
+                g.replay()
+            e1.record(stream)
+            stream.synchronize()
+        step_ms[t] = e0.elapsed_time(e1) / 3
+        del g
+    best_step = min(step_ms, key=step_ms.get)
+    api.pip_set_tuning(*best_step)
+    autotuned["step"] = {"best": list(best_step), "ms": {",".join(map(str, k)): v for k, v in step_ms.items()}}
     m = np.diff(po.astype(np.int64))
     T = sum(int((m * np.diff(c.cpu().numpy().astype(np.int64))).sum()) for c in co)
     C = sum(int(c[-1].item()) for c in co)
