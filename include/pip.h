@@ -98,9 +98,11 @@ typedef struct pip_stats {
  * 32-bit differences; otherwise the side test (p - R_i) . n runs in FP32 with a proven
  * forward-error bound, and any candidate with a (point, edge) pair whose FP32 value lies
  * within the bound is re-tested exactly with 64/128-bit integers.  The result is exact
- * either way.  Polygons of up to 256 vertices run in a kernel where each warp takes runs of
- * consecutive polygons; larger ones (or those with more than 2^18 candidate-edge pairs) in
- * a second kernel that splits their edges across CTAs (two launches on `stream`).  The
+ * either way.  Polygons of up to 256 vertices run in one of three small-polygon kernels
+ * (pip_set_small_tuning); larger ones (or those with more than 2^18 candidate-edge pairs) in
+ * a second kernel that splits their edges across CTAs in tiles, each tile taking the 32-bit
+ * test when its own vertices span a box small enough, else the FP32 filter in the tile's
+ * frame (two launches on `stream`).  The
  * first call on a stream allocates that stream's work list and must not be captured.
  * Arguments and output layout as described above.  Returns PIP_OK or PIP_ERR_*.
  */
