@@ -182,9 +182,9 @@ int pip_classify_slab(const int32_t *points, int64_t n_points,
  * pip_classify_noalloc -- pip_classify for callers that cannot allocate device memory (the
  * paper has no counterpart).  pip_classify allocates, on its first call on each stream, the
  * device list that hands large polygons to its second kernel (and, once per device, its
- * statistics counters).  Callers that must not trigger cudaMalloc -- code running during CUDA
- * graph capture, applications that manage all device memory through their own allocator or a
- * fixed budget, paths that cannot afford cudaMalloc's implicit synchronisation -- can call
+ * statistics counters).  Callers that must not trigger cudaMalloc -- applications that
+ * manage all device memory through their own allocator or a fixed budget, paths that cannot
+ * afford cudaMalloc's implicit synchronisation -- can call
  * this variant instead: same arguments, same bits, same kernels, but the list lives in a
  * fixed array inside the library's device image (512 KiB per device, held until the process
  * exits), so no call allocates.

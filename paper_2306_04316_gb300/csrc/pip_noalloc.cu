@@ -3,9 +3,9 @@
 // pip_classify keeps the list of polygons that go to its large-polygon kernel in memory the
 // library allocates with cudaMalloc on the first call on each stream (and its statistics
 // counters on the first call on each device).  Some callers cannot let a library do that:
-// code that runs while a CUDA graph is being captured, applications that own every byte of
-// device memory through their own allocator or a fixed budget, and latency-critical paths
-// where the implicit synchronisation of cudaMalloc is not acceptable.  This entry point
+// applications that own every byte of device memory through their own allocator or a fixed
+// budget, and latency-critical paths where the implicit synchronisation of cudaMalloc is not
+// acceptable.  This entry point
 // classifies with the same kernels but takes that list, and its statistics counters, from a
 // fixed array in the library's own device image (below), so it never allocates: no cudaMalloc,
 // cudaFree or allocating library routine is called on its path.  The paper has no counterpart; the limit is

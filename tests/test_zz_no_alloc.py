@@ -1,7 +1,7 @@
 """pip_classify_noalloc: the entry point for callers that cannot allocate device memory.
 
-Some callers cannot let a library call cudaMalloc (graph capture, their own allocator or a
-fixed memory budget, paths that cannot take its synchronisation).  pip_classify_noalloc keeps
+Some callers cannot let a library call cudaMalloc (their own allocator or a fixed memory
+budget, paths that cannot take its synchronisation).  pip_classify_noalloc keeps
 its scratch -- the list of large polygons -- in a fixed array inside the library instead.
 This file is collected last so that a failure here leaves every other test already run.
 The test calls the entry point through the C ABI on two calls in a row (the array keeps the
