@@ -98,6 +98,25 @@ def test_tuning_validation(lib):
     assert lib.pip_set_tuning(*before) == 0
 
 
+def test_autotuner_grids_are_valid_tunings(lib):
+    """Every shape the autotuners (and the bench's per-workload and join-step searches) may apply
+    is one the library accepts, so a search never stops on PIP_ERR_INVALID."""
+    from paper_2306_04316_gb300 import tuning
+    s = [ctypes.c_int32() for _ in range(3)]
+    t = [ctypes.c_int32() for _ in range(3)]
+    assert lib.pip_get_small_tuning(*[ctypes.byref(x) for x in s]) == 0
+    assert lib.pip_get_tuning(*[ctypes.byref(x) for x in t]) == 0
+    try:
+        for shape in tuning.DEFAULT_GRID + [(256, 4, 3), (512, 4, 3), (512, 2, 2), (1024, 4, 3), (2048, 4, 3),
+                                            (4096, 4, 2)]:
+            assert lib.pip_set_tuning(*shape) == 0, shape
+        for shape in tuning.SMALL_GRID:
+            assert lib.pip_set_small_tuning(*shape) == 0, shape
+    finally:
+        assert lib.pip_set_tuning(*[x.value for x in t]) == 0
+        assert lib.pip_set_small_tuning(*[x.value for x in s]) == 0
+
+
 def test_bin_workspace_size_grows(lib):
     """The binning workspace holds the polygons' boxes, cell table and lists (at least a 16-byte
     box, two 8-byte slots and a list entry per polygon) and the recorded (polygon, point) pairs
